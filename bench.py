@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark: Hari-Zimmermann GHSVD solves/s on one LAPW-shaped pencil.
+
+Workload (one "step" = one complete solve, every sweep of the hot path):
+complex128 F 3072 x 2048 with J = diag(+1 x 2560, -1 x 512), G 4096 x 2048
+with log-uniform singular values (cond(S) = 1e10), block width 32 (64 block
+columns, 32 block pairs per step, 63 steps per sweep), FP64 sweeps until no
+big transformation (arXiv 1907.08560, Section 6.4).  Synthetic, seeded data
+(the paper's LAPW datasets are not available).  The inputs (235 MB) are
+larger than the 129 MB L2, so no explicit flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun (N > 1) every rank solves its own copy of the pencil (weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HZ GHSVD solves/s at n=2048 c128"
+N, M, P, M_MINUS, W_BLOCK = 2048, 3072, 4096, 512, 32
+SEED = 1907085600 + 2
+# Outer sweeps the FP64 GPU solve of this pencil takes (measured; the CPU
+# reference arm extrapolates its timed sample with it).
+SWEEPS_PER_SOLVE = 20
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+
+
+def flops_per_sweep(n=N, m=M, p=P, w=W_BLOCK):
+    """Algorithmic real flops of one block sweep (round-robin over nb block
+    columns of width w): Hermitian block Grams over the m + p rows plus the
+    block update of the m + p + n rows of F, G, Z' (complex MAC = 8 flops)."""
+    nb = n // w
+    pairs = nb * (nb - 1) // 2
+    k = 2 * w
+    return 8 * pairs * (k * (k + 1) // 2 * (m + p) + k * k * (m + p + n))
+
+
+def update_flops_per_launch(n=N, m=M, p=P, w=W_BLOCK):
+    """One update launch: nb/2 block pairs, (m+p+n) rows x 2w x 2w complex MACs."""
+    nb = n // w
+    return 8 * (nb // 2) * (m + p + n) * (2 * w) ** 2
+
+
+def gram_flops_per_launch(n=N, m=M, p=P, w=W_BLOCK):
+    nb = n // w
+    k = 2 * w
+    return 8 * (nb // 2) * k * (k + 1) // 2 * (m + p)
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def make_pencil():
+    from synth import pencils
+    return pencils.lapw_pencil(N, SEED)
+
+
+def traffic_per_launch():
+    """DRAM bytes per update launch from the committed ncu capture, or None
+    when the kernel source changed since the capture."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+        src = os.path.join(ROOT, "paper_1907_08560_gb300", "csrc", rec["source"])
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if digest != rec["sha256"]:
+            return None
+        return rec["bytes_per_launch"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(F, G, J, sweeps, target_s=12.0):
+    """The FP64 oracle (blocked, OpenMP over the block pairs of a step) on the
+    host cores: time consecutive outer steps of the first sweep until
+    target_s seconds, scale to a whole solve (63 steps/sweep x sweeps)."""
+    import oracle
+    nthreads = os.cpu_count() or 1
+    t_step, steps = oracle.time_blocked_steps(F, G, J, w=W_BLOCK, target_s=target_s,
+                                              nthreads=nthreads)
+    steps_per_sweep = N // W_BLOCK - 1
+    solve_s = t_step * steps_per_sweep * sweeps
+    return {"value": 1.0 / solve_s, "unit": "solves/s", "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": (f"{steps} outer steps (32 block pairs each) of sweep 1 of the FP64 "
+                       f"blocked oracle on this pencil, {t_step:.3f} s/step, scaled by "
+                       f"{steps_per_sweep} steps/sweep x {sweeps} sweeps")}
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    F, J, G = make_pencil()
+    import oracle
+    oracle.build()
+    nthreads = os.cpu_count() or 1
+    steps_per_sweep = N // W_BLOCK - 1
+    for _ in range(args.warmup):
+        oracle.time_blocked_steps(F, G, J, w=W_BLOCK, target_s=0.0, nthreads=nthreads, max_steps=1)
+    t_step, steps = oracle.time_blocked_steps(F, G, J, w=W_BLOCK, target_s=0.0,
+                                              nthreads=nthreads, max_steps=args.steps)
+    solve_s = t_step * steps_per_sweep * SWEEPS_PER_SOLVE
+    value = 1.0 / solve_s
+    sample = (f"each step: one outer step (32 block pairs) of the FP64 blocked oracle at n=2048 "
+              f"on {oracle.max_threads()} host threads ({t_step:.3f} s); solve time extrapolated "
+              f"x {steps_per_sweep} steps/sweep x {SWEEPS_PER_SOLVE} sweeps")
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "lapw_pencil n=2048 m=3072 p=4096 J 2560+/512- cond(S)=1e10 w=32",
+                       "precision": "fp64", "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": oracle.max_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_1907_08560_gb300 import build as libbuild
+    from paper_1907_08560_gb300 import ghsvd
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    libbuild.build()
+    libbuild.build_peak()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def allreduce(x, op):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=op)
+        return t.item()
+
+    F, J, G = make_pencil()
+    Fd = ghsvd.colmajor(torch.from_numpy(F)).cuda()
+    Gd = ghsvd.colmajor(torch.from_numpy(G)).cuda()
+    Jd = torch.from_numpy(J).cuda()
+    prec = ghsvd.GHSVD_PRECISION_MIXED if args.precision == "mixed" else ghsvd.GHSVD_PRECISION_FP64
+    solver = ghsvd.Solver(local, block_width=W_BLOCK, precision=prec, timing=1)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        solver.solve(Fd, Gd, Jd, stream=stream)
+    torch.cuda.synchronize()
+
+    acc = dict(ms_update=0.0, launches_update=0, ms_gram=0.0, launches_gram=0, ms_inner=0.0,
+               launches_inner=0, kernel_launches=0, sweeps=0)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    status = []
+    for _ in range(args.steps):
+        lam, V, sweeps, st = solver.solve(Fd, Gd, Jd, stream=stream)
+        status.append(st)
+        s = solver.stats()
+        for k in acc:
+            acc[k] += s[k]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    max_ms = allreduce(elapsed_ms, dist.ReduceOp.MAX if dist else None)
+    launches = int(allreduce(float(acc["kernel_launches"]), dist.ReduceOp.SUM if dist else None))
+    ms_per_step = max_ms / args.steps
+    value = world * args.steps / (max_ms / 1e3)
+    sweeps_per_solve = acc["sweeps"] / args.steps
+
+    # roofline of the dominant kernel (the block update): algorithmic flops
+    # per launch / mean launch time measured with events on the solve's stream
+    upd_ms = acc["ms_update"] / max(acc["launches_update"], 1)
+    gram_ms = acc["ms_gram"] / max(acc["launches_gram"], 1)
+    peak_tflops = measure_fp64_peak(local)
+    achieved = update_flops_per_launch() / (upd_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops if peak_tflops else None,
+                "traffic": traffic_per_launch(),
+                "kernel": "update_kernel<double,double>",
+                "peak_source": "FP64 DFMA measured live on this GPU (libhzpeak)",
+                "gram": {"achieved": gram_flops_per_launch() / (gram_ms * 1e-3) / 1e12,
+                         "ms_per_launch": gram_ms},
+                "inner_ms_per_launch": acc["ms_inner"] / max(acc["launches_inner"], 1),
+                "update_ms_per_launch": upd_ms,
+                "whole_solve_tflops": flops_per_sweep() * sweeps_per_solve / (ms_per_step * 1e-3) / 1e12}
+
+    # end to end through the host-memory entry point (pinned buffers)
+    e2e = None
+    if args.e2e_steps > 0:
+        Fp = np.asfortranarray(F)
+        Gp = np.asfortranarray(G)
+        Fpin = torch.empty(Fp.size, dtype=torch.complex128).pin_memory()
+        Gpin = torch.empty(Gp.size, dtype=torch.complex128).pin_memory()
+        Fpin.numpy()[:] = Fp.ravel(order="F")
+        Gpin.numpy()[:] = Gp.ravel(order="F")
+        lam_pin = torch.empty(N, dtype=torch.float64).pin_memory()
+        V_pin = torch.empty(N * N, dtype=torch.complex128).pin_memory()
+        Jpin = torch.from_numpy(J.copy()).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            st = solver_host(ghsvd, solver, Fpin, Gpin, Jpin, lam_pin, V_pin)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        t_e2e = allreduce(t_e2e, dist.ReduceOp.MAX if dist else None)
+        e2e = {"value": world * args.e2e_steps / t_e2e, "unit": "solves/s",
+               "h2d_bytes_per_step": (M * N + P * N) * 16 + M,
+               "d2h_bytes_per_step": N * 8 + N * N * 16}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(F, G, J, round(sweeps_per_solve))
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": "lapw_pencil n=2048 m=3072 p=4096 J 2560+/512- "
+                                       "cond(S)=1e10 w=32",
+                           "precision": args.precision, "sweeps_per_solve": sweeps_per_solve,
+                           "status": status, "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (235 MB)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def solver_host(ghsvd, solver, Fpin, Gpin, Jpin, lam_pin, V_pin):
+    import ctypes
+    sweeps = ctypes.c_int(0)
+    lib = ghsvd.load()
+    s = lib.ghsvd_solve_host(solver.h, M, P, N, Fpin.data_ptr(), M, Jpin.data_ptr(), 0,
+                             Gpin.data_ptr(), P, lam_pin.data_ptr(), V_pin.data_ptr(), N,
+                             ctypes.byref(sweeps), None)
+    return s
+
+
+def measure_fp64_peak(device):
+    import ctypes
+    from paper_1907_08560_gb300 import build as libbuild
+    lib = ctypes.CDLL(libbuild.PEAK_LIB)
+    lib.hzpeak_fp64_tflops.restype = ctypes.c_int
+    lib.hzpeak_fp64_tflops.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    t = ctypes.c_double(0.0)
+    rc = lib.hzpeak_fp64_tflops(device, ctypes.byref(t))
+    return t.value if rc == 0 else None
+
+
+if __name__ == "__main__":
+    main()

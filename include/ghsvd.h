@@ -1,0 +1,171 @@
+/*
+ * ghsvd.h -- C ABI of the GB300 (sm_103a) implicit one-sided Hari-Zimmermann
+ * solver for the generalized hyperbolic SVD (GHSVD) of a complex pair (F, G)
+ * under a signature J (Singer, Di Napoli, Novakovic, Caklovic, "The LAPW
+ * method with eigendecomposition based on the Hari-Zimmermann generalized
+ * hyperbolic SVD", arXiv 1907.08560).
+ *
+ * Given F (m x n, m >= n), J = diag(+-1) (m x m) and G (p x n) of full column
+ * rank (hence p >= n), the solver computes the generalized eigenvalues and
+ * S-orthonormal eigenvectors of the definite pencil (H, S) = (F^* J F, G^* G)
+ * (Section 3, Definition 3.1 and eq. 3.2) without forming H or S and without
+ * a Cholesky factorization: block column pairs of F and G are transformed in
+ * place by the Level-2 block HZ method of Section 6.4 until no "big"
+ * transformation remains (Section 6.1.7).
+ *
+ * Conventions shared by every entry point:
+ *   - complex numbers are complex128 (two doubles, real part first);
+ *     matrices are column-major with a leading dimension ld >= rows;
+ *   - "device" pointers are CUDA device memory of the handle's device,
+ *     "host" pointers are ordinary (pageable or pinned) host memory;
+ *   - inputs are caller-owned and never modified; outputs are
+ *     caller-allocated; the library owns only its working buffers, which it
+ *     allocates on the first solve and reuses while the sizes fit;
+ *   - every call is ordered on the given CUDA stream (NULL: the legacy
+ *     default stream) and returns only after the result is complete, since
+ *     the sweep loop reads the transformation counters on the host once per
+ *     sweep;
+ *   - no C++ exception crosses this boundary; every failure is a status.
+ */
+#ifndef GHSVD_H
+#define GHSVD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ghsvd_ctx *ghsvd_t;
+
+typedef enum {
+    GHSVD_OK = 0,
+    GHSVD_ERR_INVALID_ARG = 1,     /* bad size, ld, pointer or J entry          */
+    GHSVD_ERR_RANK_DEFICIENT = 2,  /* a pivot of G numerically dependent (x >= 1
+                                      or g_j^* g_j <= 0), Section 6.4.2       */
+    GHSVD_ERR_NONFINITE = 3,       /* NaN/Inf in the inputs or the iteration    */
+    GHSVD_ERR_NOT_CONVERGED = 4,   /* max_sweeps reached; outputs still written */
+    GHSVD_ERR_CUDA = 5,            /* a CUDA runtime error                      */
+    GHSVD_ERR_NOMEM = 6            /* device allocation failed                  */
+} ghsvd_status;
+
+/* Precision schedules. */
+#define GHSVD_PRECISION_FP64 0     /* every sweep in complex128 / FP64            */
+#define GHSVD_PRECISION_MIXED 1    /* complex64 preconditioning sweeps with FP32
+                                      accumulation, then FP64 finishing sweeps;
+                                      the 2x2 parameters, J-norms and the
+                                      stopping test are always FP64            */
+
+typedef struct {
+    int block_width;     /* w: maximal block-column width, 1..32 (Section 6.4.1);
+                            default 32                                        */
+    int inner_sweeps;    /* inner sweeps per block pivot: 1 = BO (default),
+                            up to 30 = FB (Section 6.4.2)                     */
+    int max_sweeps;      /* C_max for the outer (block) sweeps, default 30
+                            (Algorithm 1)                                      */
+    int crit_mode;       /* eq. 6.12 reading: 0 = |h_pq| >= sqrt(max) eps
+                            sqrt(n) sqrt(min) (default), 1 = as printed       */
+    int precision;       /* GHSVD_PRECISION_FP64 (default) or _MIXED           */
+    int mixed_max_sweeps;/* at most this many complex64 sweeps (default 24)    */
+    int sort_ascending;  /* 1: sort lambda ascending and permute V alike;
+                            0 (default): column order of the iteration, as in
+                            the paper (Section 3)                              */
+    int gram_chunk;      /* rows per Gram work unit; 0 = automatic            */
+    int timing;          /* 1: time every step kernel with CUDA events on the
+                            solve's stream (ghsvd_stats.ms_*); 0 (default): off */
+} ghsvd_opts;
+
+/* Per-solve statistics (Section 6.4.3, "Completing a sweep"). */
+typedef struct {
+    int sweeps;                    /* outer sweeps run (all precisions)          */
+    int sweeps_low;                /* of which complex64 (mixed schedule)        */
+    int steps_per_sweep;           /* outer round-robin steps per sweep          */
+    int pairs_per_step;            /* block column pairs per step                */
+    int block_width;               /* widest block column actually used          */
+    long long transforms[64];      /* all transformations, per sweep (first 64)  */
+    long long big[64];             /* big transformations, per sweep             */
+    double ms_total;               /* wall time of the last solve, ms            */
+    long long kernel_launches;     /* kernels this library launched in the solve */
+    long long launches_gram, launches_inner, launches_update;
+    double ms_gram, ms_inner, ms_update;   /* summed device time (timing = 1)     */
+} ghsvd_stats;
+
+/* Fill *opts with the defaults listed above. */
+ghsvd_status ghsvd_default_opts(ghsvd_opts *opts);
+
+/* Create a solver handle on CUDA device `device` with options `opts`
+ * (NULL: defaults).  Allocates nothing on the device yet.  *h receives the
+ * handle, or NULL on error. */
+ghsvd_status ghsvd_create(ghsvd_t *h, int device, const ghsvd_opts *opts);
+
+/*
+ * Solve H z = lambda S z for H = F^* J F, S = G^* G (eq. 3.2).
+ *   m, p, n   sizes: m >= n >= 1, p >= n.
+ *   F, ldf    device, complex128 m x n, ld ldf >= m; read only.
+ *   J         device or host int8, m entries each +1 or -1; or NULL, in which
+ *             case J = diag(+1 x n_plus, -1 x (m - n_plus)) ("positives first",
+ *             Section 4.5.1); n_plus is ignored when J != NULL.
+ *   G, ldg    device, complex128 p x n, ld ldg >= p; read only.
+ *   lambda    device, n doubles: the generalized eigenvalues
+ *             lambda_j = (f_j^* J f_j) / (g_j^* g_j) of the converged columns
+ *             (Section 6.1.7), signs following J.
+ *   V, ldv    device, complex128 n x n, ld ldv >= n, or NULL: the eigenvectors
+ *             V = Z' diag(1 / ||g'_j||), so that V^* S V = I and
+ *             V^* H V = diag(lambda) (the paper's Z up to column scaling).
+ *   sweeps    host, may be NULL: number of outer sweeps run.
+ *   stream    cudaStream_t (as void *), may be NULL.
+ * Returns GHSVD_ERR_NOT_CONVERGED if max_sweeps was reached (outputs written),
+ * GHSVD_ERR_RANK_DEFICIENT / _NONFINITE on the failures listed above
+ * (outputs undefined).
+ */
+ghsvd_status ghsvd_solve(ghsvd_t h, int64_t m, int64_t p, int64_t n,
+                         const void *F, int64_t ldf, const int8_t *J, int64_t n_plus,
+                         const void *G, int64_t ldg, double *lambda, void *V, int64_t ldv,
+                         int *sweeps, void *stream);
+
+/*
+ * As ghsvd_solve, but the accumulated transformation starts from V0
+ * (device, complex128 n x n, ld ldv0, nonsingular) instead of I: the sweeps
+ * run on (F V0, G V0) and V0 is the initial Z' (Algorithm 1 allows any
+ * initial Z' such as the prescaling D).  Used for warm starts and to resume
+ * from a saved V.
+ */
+ghsvd_status ghsvd_solve_from(ghsvd_t h, int64_t m, int64_t p, int64_t n,
+                              const void *F, int64_t ldf, const int8_t *J, int64_t n_plus,
+                              const void *G, int64_t ldg, const void *V0, int64_t ldv0,
+                              double *lambda, void *V, int64_t ldv, int *sweeps, void *stream);
+
+/*
+ * As ghsvd_solve with every array in HOST memory (F, J, G read; lambda, V
+ * written): copies in, solves, copies out.  For callers without device
+ * buffers; the copies are part of the call.
+ */
+ghsvd_status ghsvd_solve_host(ghsvd_t h, int64_t m, int64_t p, int64_t n,
+                              const void *F, int64_t ldf, const int8_t *J, int64_t n_plus,
+                              const void *G, int64_t ldg, double *lambda, void *V, int64_t ldv,
+                              int *sweeps, void *stream);
+
+/*
+ * After a solve: copy the transformed factors F' (m x n), G' (p x n) and the
+ * accumulated Z' (n x n) into device buffers (any may be NULL).  The paper's
+ * remaining outputs follow from them (Section 6.1.7): Sigma_F' and
+ * Sigma_G' are the J-norms and norms of the columns, U = F' Sigma_F'^{-1},
+ * and the left vectors of G are G' Sigma_G'^{-1}.
+ */
+ghsvd_status ghsvd_get_factors(ghsvd_t h, void *Fp, int64_t ldf, void *Gp, int64_t ldg,
+                               void *Zp, int64_t ldz, void *stream);
+
+/* Statistics of the last solve on this handle. */
+ghsvd_status ghsvd_get_stats(ghsvd_t h, ghsvd_stats *stats);
+
+/* A static, human-readable description of a status. */
+const char *ghsvd_status_string(ghsvd_status s);
+
+/* Release the handle and its device buffers (NULL is allowed). */
+void ghsvd_destroy(ghsvd_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GHSVD_H */

@@ -45,7 +45,8 @@ def _bind(lib):
                                 c_long, c_int, c_int, c_int, c_int, ctypes.POINTER(c_long), vp]
     lib.hzo_blocked_step.restype = c_long
     lib.hzo_blocked_step.argtypes = [c_long, c_long, c_long, vp, c_long, vp, vp, c_long, vp,
-                                     c_long, c_long, c_int, c_long, c_int, ctypes.POINTER(c_long)]
+                                     c_long, c_long, c_int, c_long, c_int, c_int,
+                                     ctypes.POINTER(c_long)]
     lib.hzo_block_pivot.restype = c_long
     lib.hzo_block_pivot.argtypes = [c_long, c_long, c_long, vp, c_long, vp, vp, c_long, c_long,
                                     c_int, c_long, c_long, c_int, vp, vp, vp, vp, vp,
@@ -58,6 +59,8 @@ def _bind(lib):
     lib.hzo_rr_table.restype = None
     lib.hzo_rr_table.argtypes = [c_long, vp]
     lib.hzo_max_threads.restype = c_int
+    lib.hzo_rank_check.restype = c_int
+    lib.hzo_rank_check.argtypes = [c_long, c_long, vp, c_long, vp, c_long, ctypes.POINTER(c_double)]
     lib.hzo_pivot2.restype = c_int
     lib.hzo_pivot2.argtypes = [vp, c_double, c_int, vp, ctypes.POINTER(c_int)]
     return lib
@@ -152,10 +155,39 @@ def blocked_step(F, G, J=None, Z=None, w=32, r=0, inner_sweeps=1, crit_mode=0, l
     Z = _fortran(np.eye(n) if Z is None else Z)
     nbig = ctypes.c_long(0)
     na = lib.hzo_blocked_step(m, p, n, _ptr(F), m, _ptr(Jv), _ptr(G), p, _ptr(Z), n, w,
-                              inner_sweeps, r, crit_mode, ctypes.byref(nbig))
+                              inner_sweeps, r, crit_mode, 0, ctypes.byref(nbig))
     if na < 0:
         raise RuntimeError(f"hzo_blocked_step failed: {na}")
     return F, G, Z, na, nbig.value
+
+
+def time_blocked_steps(F, G, J=None, w=32, target_s=10.0, nthreads=0, max_steps=10**9,
+                       lib=None):
+    """Run consecutive outer steps r = 0, 1, ... of the first block sweep in
+    place on copies of (F, G, I) until target_s seconds (at least one step,
+    at most max_steps); returns (mean seconds per step, steps run)."""
+    import time
+    lib = lib or load()
+    F = _fortran(F); G = _fortran(G)
+    m, n = F.shape
+    p = G.shape[0]
+    Jv = _signs(J, m)
+    Z = _fortran(np.eye(n))
+    nsteps_sweep = len(partition(n, w, lib=lib)) - 2
+    nbig = ctypes.c_long(0)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        r = steps % nsteps_sweep
+        na = lib.hzo_blocked_step(m, p, n, _ptr(F), m, _ptr(Jv), _ptr(G), p, _ptr(Z), n, w, 1, r,
+                                  0, nthreads, ctypes.byref(nbig))
+        if na < 0:
+            raise RuntimeError(f"hzo_blocked_step failed: {na}")
+        steps += 1
+        el = time.perf_counter() - t0
+        if steps >= max_steps or el >= target_s:
+            break
+    return el / steps, steps
 
 
 def block_pivot(F, G, J=None, w=32, r=0, k=0, inner_sweeps=1, crit_mode=0, lib=None):
@@ -198,14 +230,32 @@ def finalize(F, G, Z, J=None, lib=None):
     return lam, V, sf, sg
 
 
-def solve(F, G, J=None, method="pointwise", **kw):
-    """Convenience: run the oracle and finalize.  Returns dict with lam (unsorted), V, ..."""
+def rank_check(G, V, lib=None):
+    """(status, kappa_est): status -2 if G is numerically rank deficient."""
+    lib = lib or load()
+    G = _fortran(G); V = _fortran(V)
+    k = ctypes.c_double(0.0)
+    rc = lib.hzo_rank_check(G.shape[0], G.shape[1], _ptr(G), G.shape[0], _ptr(V), V.shape[0],
+                            ctypes.byref(k))
+    return rc, k.value
+
+
+def solve(F, G, J=None, method="pointwise", lib=None, **kw):
+    """Run the oracle, finalize and check the rank of G.
+
+    Returns a dict with lam (unsorted), V, the transformed factors and the
+    status (0 converged, 1 max_sweeps reached, <0 error)."""
     if method == "pointwise":
-        out = pointwise(F, G, J, **kw)
+        out = pointwise(F, G, J, lib=lib, **kw)
     else:
-        out = blocked(F, G, J, **kw)
-    lam, V, sf, sg = finalize(out["F"], out["G"], out["Z"], J)
-    out.update(lam=lam, V=V, sigma_f=sf, sigma_g=sg)
+        out = blocked(F, G, J, lib=lib, **kw)
+    if out["status"] < 0:
+        return out
+    lam, V, sf, sg = finalize(out["F"], out["G"], out["Z"], J, lib=lib)
+    rc, kappa = rank_check(G, V, lib=lib)
+    if rc < 0:
+        out["status"] = rc
+    out.update(lam=lam, V=V, sigma_f=sf, sigma_g=sg, kappa_est=kappa)
     return out
 
 

@@ -382,11 +382,56 @@ static void block_update(long len, zc *X, long ldx, long kk, const long *col,
 }
 
 /*
+ * One outer step r of the block algorithm: every block column pair (P, Q) of
+ * the step (disjoint, so processed in parallel): block pivots, inner level,
+ * block update.  Block column pair (P, Q) occupies slots [0, |P|) and
+ * [wb, wb + |Q|) of a 2*wb slot layout, wb = the widest block.  Adds the
+ * transformation counts to *n_all, *n_big; returns 0 or an error code.
+ */
+static int outer_step(long m, long p, long n, zc *F, long ldf, const signed char *J, zc *G,
+                      long ldg, zc *Z, long ldz, const long *off, long nb, int inner_sweeps,
+                      long r, double tol, int crit_mode, long *n_all_out, long *n_big_out)
+{
+    long wb = off[1] - off[0], kk = 2 * wb;
+    long n_all = 0, n_big = 0;
+    int err = 0;
+#pragma omp parallel reduction(+ : n_all, n_big) reduction(min : err)
+    {
+        zc *Hh = malloc(sizeof(zc) * kk * kk);
+        zc *Sh = malloc(sizeof(zc) * kk * kk);
+        zc *Zh = malloc(sizeof(zc) * kk * kk);
+        zc *tmp = malloc(sizeof(zc) * kk);
+        long *col = malloc(sizeof(long) * kk);
+#pragma omp for schedule(static)
+        for (long k = 0; k < nb / 2; ++k) {
+            long P, Q;
+            rr_pair(nb, r, k, &P, &Q);
+            for (long s = 0; s < kk; ++s) col[s] = -1;
+            for (long c = off[P]; c < off[P + 1]; ++c) col[c - off[P]] = c;
+            for (long c = off[Q]; c < off[Q + 1]; ++c) col[wb + c - off[Q]] = c;
+            long nbig;
+            int e;
+            long na = block_pivot(m, p, F, ldf, J, G, ldg, kk, col, tol, crit_mode,
+                                  inner_sweeps, Hh, Sh, Zh, &nbig, &e);
+            if (e < 0) { if (e < err) err = e; continue; }
+            n_all += na;
+            n_big += nbig;
+            if (na == 0) continue;             /* Z^ = I: copy only (6.4.3) */
+            block_update(m, F, ldf, kk, col, Zh, tmp);
+            block_update(p, G, ldg, kk, col, Zh, tmp);
+            block_update(n, Z, ldz, kk, col, Zh, tmp);
+        }
+        free(Hh); free(Sh); free(Zh); free(tmp); free(col);
+    }
+    *n_all_out += n_all;
+    *n_big_out += n_big;
+    return err;
+}
+
+/*
  * The Level-2 block HZ (Section 6.4).  Arguments as for hzo_pointwise, plus
  * the prescribed maximal block width w and the number of inner sweeps per
- * block pivot (1 = BO, up to 30 = FB).  Block column pair (P, Q) of an outer
- * step occupies slots [0, |P|) and [wb, wb + |Q|) of a 2*wb slot layout,
- * wb = the widest block.  Returns as hzo_pointwise.
+ * block pivot (1 = BO, up to 30 = FB).  Returns as hzo_pointwise.
  */
 int hzo_blocked(long m, long p, long n, zc *F, long ldf, const signed char *J,
                 zc *G, long ldg, zc *Z, long ldz, long w, int inner_sweeps,
@@ -399,8 +444,6 @@ int hzo_blocked(long m, long p, long n, zc *F, long ldf, const signed char *J,
     long *off = malloc(sizeof(long) * (n + 2));
     long nb = hzo_partition(n, w, off, n + 1);
     if (nb < 2) { free(off); return HZO_ERR_ARG; }
-    long wb = off[1] - off[0];
-    long kk = 2 * wb;
     double tol = eps_sqrt_n(n);
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -411,36 +454,9 @@ int hzo_blocked(long m, long p, long n, zc *F, long ldf, const signed char *J,
     int err = 0;
     for (int it = 1; it <= max_sweeps && err == 0; ++it) {
         long n_all = 0, n_big = 0;
-        for (long r = 0; r < nb - 1 && err == 0; ++r) {
-#pragma omp parallel reduction(+ : n_all, n_big) reduction(min : err)
-            {
-                zc *Hh = malloc(sizeof(zc) * kk * kk);
-                zc *Sh = malloc(sizeof(zc) * kk * kk);
-                zc *Zh = malloc(sizeof(zc) * kk * kk);
-                zc *tmp = malloc(sizeof(zc) * kk);
-                long *col = malloc(sizeof(long) * kk);
-#pragma omp for schedule(static)
-                for (long k = 0; k < nb / 2; ++k) {
-                    long P, Q;
-                    rr_pair(nb, r, k, &P, &Q);
-                    for (long s = 0; s < kk; ++s) col[s] = -1;
-                    for (long c = off[P]; c < off[P + 1]; ++c) col[c - off[P]] = c;
-                    for (long c = off[Q]; c < off[Q + 1]; ++c) col[wb + c - off[Q]] = c;
-                    long nbig;
-                    int e;
-                    long na = block_pivot(m, p, F, ldf, J, G, ldg, kk, col, tol, crit_mode,
-                                          inner_sweeps, Hh, Sh, Zh, &nbig, &e);
-                    if (e < 0) { if (e < err) err = e; continue; }
-                    n_all += na;
-                    n_big += nbig;
-                    if (na == 0) continue;             /* Z^ = I: copy only */
-                    block_update(m, F, ldf, kk, col, Zh, tmp);
-                    block_update(p, G, ldg, kk, col, Zh, tmp);
-                    block_update(n, Z, ldz, kk, col, Zh, tmp);
-                }
-                free(Hh); free(Sh); free(Zh); free(tmp); free(col);
-            }
-        }
+        for (long r = 0; r < nb - 1 && err == 0; ++r)
+            err = outer_step(m, p, n, F, ldf, J, G, ldg, Z, ldz, off, nb, inner_sweeps, r, tol,
+                             crit_mode, &n_all, &n_big);
         *sweeps = it;
         if (counts) { counts[2 * (it - 1)] = n_all; counts[2 * (it - 1) + 1] = n_big; }
         if (err < 0) break;
@@ -451,43 +467,26 @@ int hzo_blocked(long m, long p, long n, zc *F, long ldf, const signed char *J,
 }
 
 /*
- * One outer step of hzo_blocked on its own (step r of the outer round-robin
- * of the first sweep), for step-level parity checks.  Returns the number of
- * transformations applied (big ones in *nbig) or a negative error code.
+ * One outer step r (0 <= r < nb - 1) of hzo_blocked on its own, for
+ * step-level checks and for timing.  Returns the number of transformations
+ * applied (big ones in *nbig) or a negative error code.
  */
 long hzo_blocked_step(long m, long p, long n, zc *F, long ldf, const signed char *J,
                       zc *G, long ldg, zc *Z, long ldz, long w, int inner_sweeps,
-                      long r, int crit_mode, long *nbig_out)
+                      long r, int crit_mode, int nthreads, long *nbig_out)
 {
     long *off = malloc(sizeof(long) * (n + 2));
     long nb = hzo_partition(n, w, off, n + 1);
     if (nb < 2 || r < 0 || r >= nb - 1) { free(off); return HZO_ERR_ARG; }
-    long wb = off[1] - off[0], kk = 2 * wb;
-    double tol = eps_sqrt_n(n);
-    zc *Hh = malloc(sizeof(zc) * kk * kk), *Sh = malloc(sizeof(zc) * kk * kk);
-    zc *Zh = malloc(sizeof(zc) * kk * kk), *tmp = malloc(sizeof(zc) * kk);
-    long *col = malloc(sizeof(long) * kk);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
     long n_all = 0, n_big = 0;
-    int err = 0;
-    for (long k = 0; k < nb / 2; ++k) {
-        long P, Q;
-        rr_pair(nb, r, k, &P, &Q);
-        for (long s = 0; s < kk; ++s) col[s] = -1;
-        for (long c = off[P]; c < off[P + 1]; ++c) col[c - off[P]] = c;
-        for (long c = off[Q]; c < off[Q + 1]; ++c) col[wb + c - off[Q]] = c;
-        long nbig;
-        int e;
-        long na = block_pivot(m, p, F, ldf, J, G, ldg, kk, col, tol, crit_mode, inner_sweeps,
-                              Hh, Sh, Zh, &nbig, &e);
-        if (e < 0) { err = e; break; }
-        n_all += na;
-        n_big += nbig;
-        if (na == 0) continue;
-        block_update(m, F, ldf, kk, col, Zh, tmp);
-        block_update(p, G, ldg, kk, col, Zh, tmp);
-        block_update(n, Z, ldz, kk, col, Zh, tmp);
-    }
-    free(Hh); free(Sh); free(Zh); free(tmp); free(col); free(off);
+    int err = outer_step(m, p, n, F, ldf, J, G, ldg, Z, ldz, off, nb, inner_sweeps, r,
+                         eps_sqrt_n(n), crit_mode, &n_all, &n_big);
+    free(off);
     if (nbig_out) *nbig_out = n_big;
     return err < 0 ? err : n_all;
 }
@@ -578,4 +577,25 @@ int hzo_pivot2(const double *in, double tol, int crit_mode, zc *Zp, int *big)
 {
     return hzo_pivot(in[0], in[1], in[2] + I * in[3], in[4], in[5], in[6] + I * in[7],
                      tol, crit_mode, Zp, big);
+}
+
+/*
+ * Numerical rank check of G after the iteration (reading of Section 6.4.2,
+ * which stops on a rank-deficient block pivot; with the pivots transformed
+ * two-sidedly a dependent G need not show up in any 2x2 pivot, so it is
+ * detected at the end): G V has orthonormal columns, hence
+ * kappa_est = ||G||_F max_j ||v_j|| estimates cond(G) within a factor sqrt(n).
+ * Returns HZO_ERR_RANK if kappa_est > 1 / (8 eps sqrt(n)), eps = 2^-53.
+ */
+int hzo_rank_check(long p, long n, const zc *G0, long ldg, const zc *V, long ldv, double *kappa)
+{
+    double g2 = 0.0, vmax = 0.0;
+    for (long j = 0; j < n; ++j) {
+        g2 += creal(jdot(p, G0 + j * ldg, G0 + j * ldg, NULL));
+        double v2 = creal(jdot(n, V + j * ldv, V + j * ldv, NULL));
+        if (v2 > vmax) vmax = v2;
+    }
+    double k = sqrt(g2) * sqrt(vmax);
+    if (kappa) *kappa = k;
+    return (!(k <= 0.125 / (ldexp(1.0, -53) * sqrt((double)n)))) ? HZO_ERR_RANK : 0;
 }

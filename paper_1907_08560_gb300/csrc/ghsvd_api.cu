@@ -1,0 +1,617 @@
+// ghsvd_api.cu -- the C ABI of include/ghsvd.h: handle, validation, working
+// buffers, the block schedule and the sweep loop of the Level-2 block
+// Hari-Zimmermann method (arXiv 1907.08560, Section 6.4).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <vector>
+
+#include "../../include/ghsvd.h"
+#include "hz_launch.h"
+#include "hz_pivot.cuh"
+
+using hz::InnerArgs;
+using hz::StepArgs;
+
+// Per-kernel-class CUDA-event timer: events are recorded around every launch
+// on the solve's stream and read once per sweep, after the sweep's sync.
+struct KTimer {
+    std::vector<cudaEvent_t> ev;
+    int used = 0;
+    cudaError_t reserve(int count)
+    {
+        while ((int)ev.size() < count) {
+            cudaEvent_t e;
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return r;
+            ev.push_back(e);
+        }
+        return cudaSuccess;
+    }
+    void release()
+    {
+        for (auto e : ev) cudaEventDestroy(e);
+        ev.clear();
+        used = 0;
+    }
+};
+
+struct ghsvd_ctx {
+    int device = 0;
+    ghsvd_opts opts{};
+    int num_sms = 0;
+    // sizes of the allocation
+    long long cap_w = 0, cap_w32 = 0;   // elements of W / W32
+    long long cap_partial = 0;          // elements of the Gram partials
+    int cap_pairs = 0, cap_n = 0, cap_mpad = 0, cap_steps = 0;
+    // device buffers
+    double2 *W = nullptr;               // [Mt x n] FP64 working factors F', G', Z'
+    double2 *Wtmp = nullptr;            // [Mt x n] output of W <- W B (warm start, mixed)
+    long long cap_wtmp = 0;
+    float2 *W32 = nullptr;              // [Mt x n] complex64 copy (mixed schedule)
+    void *partial = nullptr;            // Gram partials (FP64 or FP32 pairs)
+    double2 *zhat = nullptr;            // [pairs][KKMAX^2] accumulated block transforms
+    int *pair_flag = nullptr;           // [pairs]
+    int *slotcol = nullptr;             // [steps][pairs][kk]
+    int8_t *Jrow = nullptr;             // [m_pad]
+    int8_t *Jdev = nullptr;             // [m] staging of a host J
+    unsigned long long *counters = nullptr;   // [2]
+    int *err = nullptr;                 // [2]: device error flags, bad J
+    double *lam_tmp = nullptr, *gscale = nullptr;
+    double *vnorm2 = nullptr, *gcol2 = nullptr, *kappa = nullptr;
+    int *rank = nullptr;
+    // pinned host mirrors
+    unsigned long long *h_counters = nullptr;
+    int *h_err = nullptr;
+    // state of the last solve
+    int m = 0, p = 0, n = 0, m_pad = 0, p_pad = 0, n_pad = 0;
+    long long Mt = 0;
+    bool solved = false;
+    ghsvd_stats stats{};
+    KTimer timer;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+#define CUDA_TRY(x)                                   \
+    do {                                              \
+        cudaError_t e_ = (x);                         \
+        if (e_ != cudaSuccess) return status_of(e_);  \
+    } while (0)
+
+static ghsvd_status status_of(cudaError_t e)
+{
+    if (e == cudaSuccess) return GHSVD_OK;
+    if (e == cudaErrorMemoryAllocation) return GHSVD_ERR_NOMEM;
+    return GHSVD_ERR_CUDA;
+}
+
+static long long round_up(long long x, long long r) { return (x + r - 1) / r * r; }
+
+template <typename T>
+static cudaError_t grow(T **ptr, long long count, long long *cap)
+{
+    if (*ptr && count <= *cap) return cudaSuccess;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc((void **)ptr, sizeof(T) * (size_t)std::max(count, 1LL));
+    if (e == cudaSuccess) *cap = count;
+    return e;
+}
+
+static void free_all(ghsvd_ctx *h)
+{
+    h->timer.release();
+    cudaFree(h->W); cudaFree(h->W32); cudaFree(h->Wtmp); cudaFree(h->partial); cudaFree(h->zhat);
+    cudaFree(h->pair_flag); cudaFree(h->slotcol); cudaFree(h->Jrow); cudaFree(h->Jdev);
+    cudaFree(h->counters); cudaFree(h->err); cudaFree(h->lam_tmp); cudaFree(h->gscale);
+    cudaFree(h->rank); cudaFree(h->vnorm2); cudaFree(h->gcol2); cudaFree(h->kappa);
+    cudaFreeHost(h->h_counters); cudaFreeHost(h->h_err);
+    h->W = nullptr; h->W32 = nullptr; h->Wtmp = nullptr; h->partial = nullptr; h->zhat = nullptr;
+    h->pair_flag = nullptr; h->slotcol = nullptr; h->Jrow = nullptr; h->Jdev = nullptr;
+    h->counters = nullptr; h->err = nullptr; h->lam_tmp = nullptr; h->gscale = nullptr;
+    h->rank = nullptr; h->h_counters = nullptr; h->h_err = nullptr;
+    h->vnorm2 = nullptr; h->gcol2 = nullptr; h->kappa = nullptr;
+}
+
+// Section 6.4.1: nb (even) block columns of width wb or wb - 1, widths
+// non-increasing, from the prescribed maximal width w.
+static int partition(int n, int w, std::vector<int> &off)
+{
+    int nb = (n + w - 1) / w;
+    if (nb & 1) nb += 1;
+    if (nb < 2) nb = 2;
+    if (nb > n) nb = n & ~1;
+    const int wb = (n + nb - 1) / nb;
+    const int wide = n - nb * (wb - 1);
+    off.assign(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) off[b + 1] = off[b] + (b < wide ? wb : wb - 1);
+    return nb;
+}
+
+// Gram chunk: the multiple of GRAM_KT rows that balances the per-step Gram
+// CTAs over the SMs best (ties: the larger chunk, fewer partials to sum).
+static int choose_chunk(int m_pad, int p_pad, int npairs, int sms, int forced)
+{
+    if (forced > 0) return (int)round_up(forced, hz::GRAM_KT);
+    long long best_cost = -1;
+    int best = 512;
+    for (int kc = 128; kc <= 4096; kc += 64) {
+        const long long ch = (m_pad + kc - 1) / kc + (p_pad + kc - 1) / kc;
+        const long long ctas = ch * npairs;
+        const long long waves = (ctas + sms - 1) / sms;
+        // time ~ waves * kc + partial-sum work in the inner kernel
+        const long long cost = waves * kc + ch * 8;
+        if (best_cost < 0 || cost < best_cost || (cost == best_cost && kc > best)) {
+            best_cost = cost;
+            best = kc;
+        }
+    }
+    return best;
+}
+
+static bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+ghsvd_status ghsvd_default_opts(ghsvd_opts *o)
+{
+    if (!o) return GHSVD_ERR_INVALID_ARG;
+    memset(o, 0, sizeof(*o));
+    o->block_width = 32;
+    o->inner_sweeps = 1;
+    o->max_sweeps = 30;
+    o->crit_mode = 0;
+    o->precision = GHSVD_PRECISION_FP64;
+    o->mixed_max_sweeps = 24;
+    o->sort_ascending = 0;
+    o->gram_chunk = 0;
+    o->timing = 0;
+    return GHSVD_OK;
+}
+
+const char *ghsvd_status_string(ghsvd_status s)
+{
+    switch (s) {
+    case GHSVD_OK: return "ok";
+    case GHSVD_ERR_INVALID_ARG: return "invalid argument";
+    case GHSVD_ERR_RANK_DEFICIENT: return "G is numerically rank deficient";
+    case GHSVD_ERR_NONFINITE: return "non-finite value in the input or the iteration";
+    case GHSVD_ERR_NOT_CONVERGED: return "not converged within max_sweeps";
+    case GHSVD_ERR_CUDA: return "CUDA error";
+    case GHSVD_ERR_NOMEM: return "out of device memory";
+    }
+    return "unknown status";
+}
+
+ghsvd_status ghsvd_create(ghsvd_t *out, int device, const ghsvd_opts *opts)
+{
+    if (!out) return GHSVD_ERR_INVALID_ARG;
+    *out = nullptr;
+    ghsvd_opts o;
+    if (opts) o = *opts;
+    else ghsvd_default_opts(&o);
+    if (o.block_width < 1 || o.block_width > hz::KKMAX / 2 || o.inner_sweeps < 1 ||
+        o.inner_sweeps > 30 || o.max_sweeps < 1 || o.max_sweeps > 1000 ||
+        (o.crit_mode != 0 && o.crit_mode != 1) ||
+        (o.precision != GHSVD_PRECISION_FP64 && o.precision != GHSVD_PRECISION_MIXED) ||
+        o.mixed_max_sweeps < 0 || o.gram_chunk < 0 || (o.timing != 0 && o.timing != 1))
+        return GHSVD_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return GHSVD_ERR_INVALID_ARG;
+    }
+    ghsvd_ctx *h = new (std::nothrow) ghsvd_ctx();
+    if (!h) return GHSVD_ERR_NOMEM;
+    h->device = device;
+    h->opts = o;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = hz::setup_kernels();
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_counters, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_err, 2 * sizeof(int));
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        free_all(h);
+        delete h;
+        return status_of(e);
+    }
+    *out = h;
+    return GHSVD_OK;
+}
+
+void ghsvd_destroy(ghsvd_t h)
+{
+    if (!h) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    free_all(h);
+    cudaSetDevice(prev);
+    delete h;
+}
+
+ghsvd_status ghsvd_get_stats(ghsvd_t h, ghsvd_stats *s)
+{
+    if (!h || !s) return GHSVD_ERR_INVALID_ARG;
+    *s = h->stats;
+    return GHSVD_OK;
+}
+
+}  // extern "C"
+
+// The solver proper.  Dptr arguments are device pointers (validated by the
+// callers of this function).
+static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64, const void *F,
+                               int64_t ldf, const int8_t *J, int64_t n_plus, const void *G,
+                               int64_t ldg, const void *V0, int64_t ldv0, double *lambda, void *V,
+                               int64_t ldv, int *sweeps_out, cudaStream_t st)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const ghsvd_opts &o = h->opts;
+    const int m = (int)m64, p = (int)p64, n = (int)n64;
+    const int m_pad = (int)round_up(m, hz::ROWPAD), p_pad = (int)round_up(p, hz::ROWPAD);
+    const int n_pad = (int)round_up(n, hz::ROWPAD);
+    const long long Mt = (long long)m_pad + p_pad + n_pad;
+    h->solved = false;
+    memset(&h->stats, 0, sizeof(h->stats));
+
+    // schedule (Section 6.3, 6.4.1)
+    std::vector<int> off;
+    int nb = 0, wb = 1, kk = 2, npairs = 0, nsteps = 0;
+    if (n >= 2) {
+        nb = partition(n, std::min(o.block_width, n), off);
+        wb = off[1] - off[0];
+        kk = 2 * wb;
+        npairs = nb / 2;
+        nsteps = nb - 1;
+    }
+    const bool mixed = o.precision == GHSVD_PRECISION_MIXED && n >= 2;
+    const int kc = n >= 2 ? choose_chunk(m_pad, p_pad, npairs, h->num_sms, o.gram_chunk) : 16;
+    const int chunks_h = (m_pad + kc - 1) / kc, chunks_s = (p_pad + kc - 1) / kc;
+    const int cpp = chunks_h + chunks_s;
+
+    // buffers
+    long long cap;
+    CUDA_TRY(grow(&h->W, Mt * n, &h->cap_w));
+    if (mixed) CUDA_TRY(grow(&h->W32, Mt * n, &h->cap_w32));
+    const long long npart = (long long)std::max(npairs, 1) * cpp * hz::KKMAX * hz::KKMAX;
+    {
+        double2 *pp = (double2 *)h->partial;
+        CUDA_TRY(grow(&pp, npart, &h->cap_partial));
+        h->partial = pp;
+    }
+    if (npairs > h->cap_pairs || h->zhat == nullptr) {
+        cudaFree(h->zhat); cudaFree(h->pair_flag);
+        h->zhat = nullptr; h->pair_flag = nullptr;
+        CUDA_TRY(cudaMalloc((void **)&h->zhat, sizeof(double2) * std::max(npairs, 1) * hz::KKMAX * hz::KKMAX));
+        CUDA_TRY(cudaMalloc((void **)&h->pair_flag, sizeof(int) * std::max(npairs, 1)));
+        h->cap_pairs = std::max(npairs, 1);
+    }
+    cap = (long long)h->cap_steps;
+    if ((long long)std::max(nsteps, 1) * std::max(npairs, 1) * kk > cap || !h->slotcol) {
+        cudaFree(h->slotcol);
+        h->slotcol = nullptr;
+        const long long cnt = (long long)std::max(nsteps, 1) * std::max(npairs, 1) * kk;
+        CUDA_TRY(cudaMalloc((void **)&h->slotcol, sizeof(int) * cnt));
+        h->cap_steps = (int)cnt;
+    }
+    if (m_pad > h->cap_mpad || !h->Jrow) {
+        cudaFree(h->Jrow); cudaFree(h->Jdev);
+        h->Jrow = nullptr; h->Jdev = nullptr;
+        CUDA_TRY(cudaMalloc((void **)&h->Jrow, m_pad));
+        CUDA_TRY(cudaMalloc((void **)&h->Jdev, m_pad));
+        h->cap_mpad = m_pad;
+    }
+    if (n > h->cap_n || !h->lam_tmp) {
+        cudaFree(h->lam_tmp); cudaFree(h->gscale); cudaFree(h->rank);
+        cudaFree(h->vnorm2); cudaFree(h->gcol2);
+        h->lam_tmp = nullptr; h->gscale = nullptr; h->rank = nullptr;
+        h->vnorm2 = nullptr; h->gcol2 = nullptr;
+        CUDA_TRY(cudaMalloc((void **)&h->vnorm2, sizeof(double) * n));
+        CUDA_TRY(cudaMalloc((void **)&h->gcol2, sizeof(double) * n));
+        CUDA_TRY(cudaMalloc((void **)&h->lam_tmp, sizeof(double) * n));
+        CUDA_TRY(cudaMalloc((void **)&h->gscale, sizeof(double) * n));
+        CUDA_TRY(cudaMalloc((void **)&h->rank, sizeof(int) * n));
+        h->cap_n = n;
+    }
+    if (!h->counters) {
+        CUDA_TRY(cudaMalloc((void **)&h->counters, 2 * sizeof(unsigned long long)));
+        CUDA_TRY(cudaMalloc((void **)&h->err, 2 * sizeof(int)));
+        CUDA_TRY(cudaMalloc((void **)&h->kappa, sizeof(double)));
+    }
+
+    // slot tables: step r, pair k -> block pair (P, Q) of the round-robin over
+    // nb blocks; P's columns in slots [0, |P|), Q's in [wb, wb + |Q|)
+    if (n >= 2) {
+        std::vector<int> tab((size_t)nsteps * npairs * kk, -1);
+        for (int r = 0; r < nsteps; ++r)
+            for (int k = 0; k < npairs; ++k) {
+                int P, Q;
+                hz::rr_pair(nb, r, k, &P, &Q);
+                int *row = &tab[((size_t)r * npairs + k) * kk];
+                for (int c = off[P]; c < off[P + 1]; ++c) row[c - off[P]] = c;
+                for (int c = off[Q]; c < off[Q + 1]; ++c) row[wb + c - off[Q]] = c;
+            }
+        CUDA_TRY(cudaMemcpyAsync(h->slotcol, tab.data(), sizeof(int) * tab.size(),
+                                 cudaMemcpyHostToDevice, st));
+    }
+
+    // inputs: J (host or device) -> padded signs; [F; G; V0 or I] -> W
+    CUDA_TRY(cudaMemsetAsync(h->err, 0, 2 * sizeof(int), st));
+    const int8_t *Jd = nullptr;
+    if (J) {
+        if (is_device_ptr(J)) Jd = J;
+        else {
+            CUDA_TRY(cudaMemcpyAsync(h->Jdev, J, (size_t)m, cudaMemcpyHostToDevice, st));
+            Jd = h->Jdev;
+        }
+    }
+    CUDA_TRY(hz::launch_signs(h->Jrow, Jd, m, m_pad, n_plus, h->err + 1, st));
+    h->stats.kernel_launches += 3;   // signs, copy-in, column norms of G
+    CUDA_TRY(hz::launch_copyin(h->W, false, Mt, m, p, n, m_pad, p_pad, n_pad, F, ldf, G, ldg,
+                               nullptr, 0, h->err, st));
+    CUDA_TRY(hz::launch_gnorm(h->W, Mt, m_pad, p_pad, n, h->gcol2, st));
+    if (V0) {
+        // warm start: the sweeps run on (F V0, G V0) and start from Z' = V0
+        // (Algorithm 1 admits any nonsingular starting Z')
+        CUDA_TRY(grow(&h->Wtmp, Mt * n, &h->cap_wtmp));
+        CUDA_TRY(hz::launch_gemm(h->W, Mt, (int)Mt, V0, false, ldv0, h->Wtmp, Mt, n, st));
+        h->stats.kernel_launches += 1;
+        CUDA_TRY(cudaMemcpyAsync(h->W, h->Wtmp, sizeof(double2) * Mt * n, cudaMemcpyDeviceToDevice, st));
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->h_err, h->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (h->h_err[1]) return GHSVD_ERR_INVALID_ARG;
+    if (h->h_err[0] & hz::DEVERR_NONFINITE) return GHSVD_ERR_NONFINITE;
+
+    h->m = m; h->p = p; h->n = n; h->m_pad = m_pad; h->p_pad = p_pad; h->n_pad = n_pad; h->Mt = Mt;
+    ghsvd_status status = GHSVD_ERR_NOT_CONVERGED;
+    int sweeps = 0, sweeps_low = 0;
+    h->stats.steps_per_sweep = nsteps;
+    h->stats.pairs_per_step = npairs;
+    h->stats.block_width = wb;
+
+    if (n < 2) {
+        status = GHSVD_OK;
+    } else {
+        StepArgs sa{};
+        sa.npairs = npairs; sa.kk = kk; sa.m_pad = m_pad; sa.p_pad = p_pad; sa.n_pad = n_pad;
+        sa.ld = Mt; sa.kc = kc; sa.chunks_h = chunks_h; sa.chunks_s = chunks_s;
+        InnerArgs ia{};
+        ia.npairs = npairs; ia.kk = kk; ia.cpp = cpp; ia.chunks_h = chunks_h;
+        ia.inner_sweeps = o.inner_sweeps; ia.crit_mode = o.crit_mode;
+        const double tol64 = ldexp(1.0, -53) * sqrt((double)n);
+        // complex64 sweeps: the single-precision unit roundoff in eq. 6.12,
+        // so that pivots below the Gram's rounding level are left alone
+        const double tol32 = ldexp(1.0, -24) * sqrt((double)n);
+
+        // mixed schedule: complex64 preconditioning sweeps on a copy of
+        // (F, G) with Z' restarted at I; their Z' is then applied to the FP64
+        // factors (W <- W Z'_low) and FP64 sweeps finish the iteration
+        int phase_single = mixed ? 1 : 0;
+        if (mixed) {
+            CUDA_TRY(hz::launch_convert(h->W32, true, h->W, Mt * n, st));
+            CUDA_TRY(hz::launch_eye32(h->W32, Mt, m_pad + p_pad, n, n_pad, st));
+            h->stats.kernel_launches += 2;
+            CUDA_TRY(grow(&h->Wtmp, Mt * n, &h->cap_wtmp));
+        }
+        while (sweeps < o.max_sweeps) {
+            const bool single = phase_single != 0;
+            ia.tol = single ? tol32 : tol64;
+            void *Wc = single ? (void *)h->W32 : (void *)h->W;
+            CUDA_TRY(cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned long long), st));
+            const bool timed = o.timing != 0;
+            if (timed) CUDA_TRY(h->timer.reserve(6 * nsteps));
+            cudaEvent_t *ev = timed ? h->timer.ev.data() : nullptr;
+            for (int r = 0; r < nsteps; ++r) {
+                sa.slotcol = h->slotcol + (size_t)r * npairs * kk;
+                if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 0], st));
+                CUDA_TRY(hz::launch_gram(Wc, single, h->Jrow, sa, h->partial, st));
+                if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 1], st));
+                if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 2], st));
+                CUDA_TRY(hz::launch_inner(h->partial, single, sa.slotcol, ia, h->zhat, h->pair_flag,
+                                          h->counters, h->err, st));
+                if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 3], st));
+                if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 4], st));
+                CUDA_TRY(hz::launch_update(Wc, single, sa, h->zhat, h->pair_flag, st));
+                if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 5], st));
+            }
+            h->stats.launches_gram += nsteps;
+            h->stats.launches_inner += nsteps;
+            h->stats.launches_update += nsteps;
+            h->stats.kernel_launches += 3LL * nsteps;
+            CUDA_TRY(cudaMemcpyAsync(h->h_counters, h->counters, 2 * sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaMemcpyAsync(h->h_err, h->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            if (timed) {
+                for (int r = 0; r < nsteps; ++r) {
+                    float a = 0, b = 0, c = 0;
+                    CUDA_TRY(cudaEventElapsedTime(&a, ev[6 * r + 0], ev[6 * r + 1]));
+                    CUDA_TRY(cudaEventElapsedTime(&b, ev[6 * r + 2], ev[6 * r + 3]));
+                    CUDA_TRY(cudaEventElapsedTime(&c, ev[6 * r + 4], ev[6 * r + 5]));
+                    h->stats.ms_gram += a;
+                    h->stats.ms_inner += b;
+                    h->stats.ms_update += c;
+                }
+            }
+            if (sweeps < 64) {
+                h->stats.transforms[sweeps] = (long long)h->h_counters[0];
+                h->stats.big[sweeps] = (long long)h->h_counters[1];
+            }
+            ++sweeps;
+            if (single) ++sweeps_low;
+            if (h->h_err[0] & hz::DEVERR_RANK) { status = GHSVD_ERR_RANK_DEFICIENT; break; }
+            if (h->h_err[0] & hz::DEVERR_NONFINITE) { status = GHSVD_ERR_NONFINITE; break; }
+            if (single) {
+                // leave the complex64 phase once it stops making big progress
+                // or its sweep budget is spent; the FP64 phase restarts from
+                // the original F, G transformed by the accumulated Z'
+                const bool done = h->h_counters[0] == 0 || sweeps_low >= o.mixed_max_sweeps;
+                if (done) {
+                    phase_single = 0;
+                    const float2 *zlow = h->W32 + (m_pad + p_pad);
+                    CUDA_TRY(hz::launch_gemm(h->W, Mt, (int)Mt, zlow, true, Mt, h->Wtmp, Mt, n, st));
+                    h->stats.kernel_launches += 1;
+                    CUDA_TRY(cudaMemcpyAsync(h->W, h->Wtmp, sizeof(double2) * Mt * n,
+                                             cudaMemcpyDeviceToDevice, st));
+                }
+                continue;
+            }
+            if (h->h_counters[1] == 0) { status = GHSVD_OK; break; }
+        }
+    }
+    h->stats.sweeps = sweeps;
+    h->stats.sweeps_low = sweeps_low;
+    if (status == GHSVD_ERR_RANK_DEFICIENT || status == GHSVD_ERR_NONFINITE) return status;
+
+    // outputs (Section 6.1.7)
+    CUDA_TRY(hz::launch_finalize(h->W, Mt, h->Jrow, m_pad, p_pad, n, o.sort_ascending, h->lam_tmp,
+                                 h->gscale, h->vnorm2, h->gcol2, h->kappa, h->rank, lambda,
+                                 (double2 *)V, ldv, h->err, st));
+    h->stats.kernel_launches += 4;   // column norms, rank check, order, emit
+    CUDA_TRY(cudaMemcpyAsync(h->h_err, h->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (h->h_err[0] & hz::DEVERR_RANK) return GHSVD_ERR_RANK_DEFICIENT;
+    if (h->h_err[0] & hz::DEVERR_NONFINITE) return GHSVD_ERR_NONFINITE;
+    h->solved = true;
+    if (sweeps_out) *sweeps_out = sweeps;
+    h->stats.ms_total =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return status;
+}
+
+static ghsvd_status validate(ghsvd_t h, int64_t m, int64_t p, int64_t n, const void *F, int64_t ldf,
+                             const int8_t *J, int64_t n_plus, const void *G, int64_t ldg,
+                             double *lambda, const void *V, int64_t ldv)
+{
+    if (!h || !F || !G || !lambda) return GHSVD_ERR_INVALID_ARG;
+    if (n < 1 || m < n || p < n) return GHSVD_ERR_INVALID_ARG;
+    if (m > (1LL << 30) || p > (1LL << 30) || n > (1 << 20)) return GHSVD_ERR_INVALID_ARG;
+    if (ldf < m || ldg < p) return GHSVD_ERR_INVALID_ARG;
+    if (V && ldv < n) return GHSVD_ERR_INVALID_ARG;
+    if (!J && (n_plus < 0 || n_plus > m)) return GHSVD_ERR_INVALID_ARG;
+    return GHSVD_OK;
+}
+
+extern "C" {
+
+ghsvd_status ghsvd_solve_from(ghsvd_t h, int64_t m, int64_t p, int64_t n, const void *F, int64_t ldf,
+                              const int8_t *J, int64_t n_plus, const void *G, int64_t ldg,
+                              const void *V0, int64_t ldv0, double *lambda, void *V, int64_t ldv,
+                              int *sweeps, void *stream)
+{
+    ghsvd_status s = validate(h, m, p, n, F, ldf, J, n_plus, G, ldg, lambda, V, ldv);
+    if (s != GHSVD_OK) return s;
+    if (V0 && ldv0 < n) return GHSVD_ERR_INVALID_ARG;
+    if (!is_device_ptr(F) || !is_device_ptr(G) || !is_device_ptr(lambda) ||
+        (V && !is_device_ptr(V)) || (V0 && !is_device_ptr(V0)))
+        return GHSVD_ERR_INVALID_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(h->device) != cudaSuccess) return GHSVD_ERR_CUDA;
+    s = solve_impl(h, m, p, n, F, ldf, J, n_plus, G, ldg, V0, ldv0, lambda, V, ldv, sweeps,
+                   (cudaStream_t)stream);
+    cudaSetDevice(prev);
+    return s;
+}
+
+ghsvd_status ghsvd_solve(ghsvd_t h, int64_t m, int64_t p, int64_t n, const void *F, int64_t ldf,
+                         const int8_t *J, int64_t n_plus, const void *G, int64_t ldg, double *lambda,
+                         void *V, int64_t ldv, int *sweeps, void *stream)
+{
+    return ghsvd_solve_from(h, m, p, n, F, ldf, J, n_plus, G, ldg, nullptr, 0, lambda, V, ldv,
+                            sweeps, stream);
+}
+
+ghsvd_status ghsvd_solve_host(ghsvd_t h, int64_t m, int64_t p, int64_t n, const void *F,
+                              int64_t ldf, const int8_t *J, int64_t n_plus, const void *G,
+                              int64_t ldg, double *lambda, void *V, int64_t ldv, int *sweeps,
+                              void *stream)
+{
+    ghsvd_status s = validate(h, m, p, n, F, ldf, J, n_plus, G, ldg, lambda, V, ldv);
+    if (s != GHSVD_OK) return s;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(h->device) != cudaSuccess) return GHSVD_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *dF = nullptr, *dG = nullptr, *dV = nullptr;
+    double *dl = nullptr;
+    int8_t *dJ = nullptr;
+    cudaError_t e = cudaMallocAsync(&dF, sizeof(double2) * (size_t)m * n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dG, sizeof(double2) * (size_t)p * n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dl, sizeof(double) * (size_t)n, st);
+    if (e == cudaSuccess && V) e = cudaMallocAsync(&dV, sizeof(double2) * (size_t)n * n, st);
+    if (e == cudaSuccess && J) e = cudaMallocAsync((void **)&dJ, (size_t)m, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(dF, sizeof(double2) * m, F, sizeof(double2) * ldf, sizeof(double2) * m, n,
+                              cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(dG, sizeof(double2) * p, G, sizeof(double2) * ldg, sizeof(double2) * p, n,
+                              cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && J) e = cudaMemcpyAsync(dJ, J, (size_t)m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        s = solve_impl(h, m, p, n, dF, m, J ? dJ : nullptr, n_plus, dG, p, nullptr, 0, dl, dV, n,
+                       sweeps, st);
+        if (s == GHSVD_OK || s == GHSVD_ERR_NOT_CONVERGED) {
+            e = cudaMemcpyAsync(lambda, dl, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess && V)
+                e = cudaMemcpy2DAsync(V, sizeof(double2) * ldv, dV, sizeof(double2) * n,
+                                      sizeof(double2) * n, n, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        }
+    } else {
+        s = status_of(e);
+    }
+    cudaFreeAsync(dF, st); cudaFreeAsync(dG, st); cudaFreeAsync(dl, st);
+    if (dV) cudaFreeAsync(dV, st);
+    if (dJ) cudaFreeAsync(dJ, st);
+    cudaStreamSynchronize(st);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess && s == GHSVD_OK) s = status_of(e);
+    return s;
+}
+
+ghsvd_status ghsvd_get_factors(ghsvd_t h, void *Fp, int64_t ldf, void *Gp, int64_t ldg, void *Zp,
+                               int64_t ldz, void *stream)
+{
+    if (!h || !h->solved) return GHSVD_ERR_INVALID_ARG;
+    if ((Fp && ldf < h->m) || (Gp && ldg < h->p) || (Zp && ldz < h->n)) return GHSVD_ERR_INVALID_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(h->device) != cudaSuccess) return GHSVD_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (Fp) e = hz::launch_extract(h->W, h->Mt, 0, h->m, h->n, (double2 *)Fp, ldf, st);
+    if (e == cudaSuccess && Gp) e = hz::launch_extract(h->W, h->Mt, h->m_pad, h->p, h->n, (double2 *)Gp, ldg, st);
+    if (e == cudaSuccess && Zp)
+        e = hz::launch_extract(h->W, h->Mt, h->m_pad + h->p_pad, h->n, h->n, (double2 *)Zp, ldz, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaSetDevice(prev);
+    return status_of(e);
+}
+
+}  // extern "C"

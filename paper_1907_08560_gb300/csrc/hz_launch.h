@@ -1,0 +1,62 @@
+// hz_launch.h -- host-side launchers of the kernels in hz_step.cu.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hz {
+
+constexpr int KKMAX = 64;          // largest block pivot order 2 wb (wb <= 32)
+constexpr int ROWPAD = 64;         // row padding of each range of W
+constexpr int GRAM_KT = 16;        // rows staged per Gram step
+constexpr int UPD_R = 64;          // rows per update tile
+
+// Step descriptor passed by value to every step kernel.
+struct StepArgs {
+    const int *slotcol;     // [npairs][kk] column of each slot, -1 if empty
+    int npairs;             // block column pairs in this step
+    int kk;                 // block pivot order 2 wb
+    int m_pad, p_pad, n_pad;
+    long long ld;           // = Mt
+    int kc;                 // rows per Gram chunk (multiple of GRAM_KT)
+    int chunks_h, chunks_s; // Gram chunks over the F rows and the G rows
+};
+
+// Inner-level descriptor.
+struct InnerArgs {
+    int npairs, kk, cpp, chunks_h;
+    int inner_sweeps;                  // 1 = BO, > 1 = FB
+    int crit_mode;                     // eq. 6.12 reading
+    double tol;                        // eps * sqrt(n)
+};
+
+// Error flags raised by the device (bitwise or).
+constexpr int DEVERR_RANK = 1;
+constexpr int DEVERR_NONFINITE = 2;
+
+cudaError_t setup_kernels();
+cudaError_t launch_copyin(void *W, bool single, long long ld, int m, int p, int n, int m_pad,
+                          int p_pad, int n_pad, const void *F, long long ldf, const void *G,
+                          long long ldg, const void *V0, long long ldv0, int *err, cudaStream_t s);
+cudaError_t launch_signs(int8_t *Jrow, const int8_t *J, int m, int m_pad, long long n_plus, int *bad,
+                         cudaStream_t s);
+cudaError_t launch_convert(void *dst, bool dst_single, const void *src, long long count, cudaStream_t s);
+cudaError_t launch_gram(const void *W, bool single, const int8_t *Jrow, const StepArgs &a,
+                        void *partial, cudaStream_t s);
+cudaError_t launch_inner(const void *partial, bool single, const int *slotcol, const InnerArgs &a,
+                         double2 *zhat, int *pair_flag, unsigned long long *counters, int *err,
+                         cudaStream_t s);
+cudaError_t launch_update(void *W, bool single, const StepArgs &a, const double2 *zhat,
+                          const int *pair_flag, cudaStream_t s);
+cudaError_t launch_gnorm(const double2 *W, long long ld, int g0, int p_pad, int n, double *gcol2,
+                         cudaStream_t s);
+cudaError_t launch_finalize(const double2 *W, long long ld, const int8_t *Jrow, int m_pad, int p_pad,
+                            int n, int sort, double *lam_tmp, double *gscale, double *vnorm2,
+                            const double *gcol2, double *kappa, int *rank, double *lam_out,
+                            double2 *V, long long ldv, int *err, cudaStream_t s);
+cudaError_t launch_gemm(const double2 *A, long long lda, int rows, const void *B, bool b_single,
+                        long long ldb, double2 *C, long long ldc, int n, cudaStream_t s);
+cudaError_t launch_eye32(void *W, long long ld, int r0, int n, int n_pad, cudaStream_t s);
+cudaError_t launch_extract(const double2 *W, long long ld, int r0, int rows, int n, double2 *out,
+                           long long ldo, cudaStream_t s);
+
+}  // namespace hz

@@ -1,0 +1,272 @@
+"""Python binding of the C ABI in include/ghsvd.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA kernels of libghsvd.so; this module
+only loads the library, converts torch tensors to pointers and status codes
+to exceptions.  There is no CPU fallback: if the library is missing or no
+CUDA device is present, the calls raise.
+
+Layout: complex128 matrices are column-major.  A torch tensor ``X`` of shape
+(rows, cols) is column-major when ``X.stride() == (1, ld)``; ``colmajor``
+makes such a copy, ``ld_of`` reads the leading dimension.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libghsvd.so")
+
+GHSVD_OK = 0
+GHSVD_ERR_INVALID_ARG = 1
+GHSVD_ERR_RANK_DEFICIENT = 2
+GHSVD_ERR_NONFINITE = 3
+GHSVD_ERR_NOT_CONVERGED = 4
+GHSVD_ERR_CUDA = 5
+GHSVD_ERR_NOMEM = 6
+
+GHSVD_PRECISION_FP64 = 0
+GHSVD_PRECISION_MIXED = 1
+
+
+class ghsvd_opts(ctypes.Structure):
+    _fields_ = [("block_width", ctypes.c_int), ("inner_sweeps", ctypes.c_int),
+                ("max_sweeps", ctypes.c_int), ("crit_mode", ctypes.c_int),
+                ("precision", ctypes.c_int), ("mixed_max_sweeps", ctypes.c_int),
+                ("sort_ascending", ctypes.c_int), ("gram_chunk", ctypes.c_int),
+                ("timing", ctypes.c_int)]
+
+
+class ghsvd_stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("sweeps_low", ctypes.c_int),
+                ("steps_per_sweep", ctypes.c_int), ("pairs_per_step", ctypes.c_int),
+                ("block_width", ctypes.c_int),
+                ("transforms", ctypes.c_longlong * 64), ("big", ctypes.c_longlong * 64),
+                ("ms_total", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
+                ("launches_gram", ctypes.c_longlong), ("launches_inner", ctypes.c_longlong),
+                ("launches_update", ctypes.c_longlong), ("ms_gram", ctypes.c_double),
+                ("ms_inner", ctypes.c_double), ("ms_update", ctypes.c_double)]
+
+
+class GhsvdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libghsvd.so (it must have been built; see build.py)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libghsvd.so not built: {p} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(p)
+    vp, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.ghsvd_default_opts.restype = c_int
+    lib.ghsvd_default_opts.argtypes = [ctypes.POINTER(ghsvd_opts)]
+    lib.ghsvd_create.restype = c_int
+    lib.ghsvd_create.argtypes = [ctypes.POINTER(vp), c_int, ctypes.POINTER(ghsvd_opts)]
+    lib.ghsvd_destroy.restype = None
+    lib.ghsvd_destroy.argtypes = [vp]
+    lib.ghsvd_solve.restype = c_int
+    lib.ghsvd_solve.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, i64,
+                                ctypes.POINTER(c_int), vp]
+    lib.ghsvd_solve_from.restype = c_int
+    lib.ghsvd_solve_from.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp,
+                                     vp, i64, ctypes.POINTER(c_int), vp]
+    lib.ghsvd_solve_host.restype = c_int
+    lib.ghsvd_solve_host.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, i64,
+                                     ctypes.POINTER(c_int), vp]
+    lib.ghsvd_get_factors.restype = c_int
+    lib.ghsvd_get_factors.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp]
+    lib.ghsvd_get_stats.restype = c_int
+    lib.ghsvd_get_stats.argtypes = [vp, ctypes.POINTER(ghsvd_stats)]
+    lib.ghsvd_status_string.restype = ctypes.c_char_p
+    lib.ghsvd_status_string.argtypes = [c_int]
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def status_string(s: int) -> str:
+    return load().ghsvd_status_string(s).decode()
+
+
+def _check(s: int, allow=(GHSVD_OK,)):
+    if s not in allow:
+        raise GhsvdError(s, status_string(s))
+    return s
+
+
+def ghsvd_default_opts(**kw) -> ghsvd_opts:
+    o = ghsvd_opts()
+    _check(load().ghsvd_default_opts(ctypes.byref(o)))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, int(v))
+    return o
+
+
+def ghsvd_create(device: int = 0, opts: ghsvd_opts | None = None):
+    h = ctypes.c_void_p()
+    _check(load().ghsvd_create(ctypes.byref(h), device, ctypes.byref(opts) if opts else None))
+    return h
+
+
+def ghsvd_destroy(h) -> None:
+    if h:
+        load().ghsvd_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# torch marshalling
+# --------------------------------------------------------------------------
+
+def colmajor(X):
+    """Column-major (Fortran-order) complex128 copy of a 2-D tensor or array."""
+    import torch
+    X = torch.as_tensor(X)
+    return X.to(torch.complex128).t().contiguous().t()
+
+
+def ld_of(X) -> int:
+    if X.dim() != 2 or X.stride(0) != 1:
+        raise ValueError("expected a column-major 2-D tensor (stride (1, ld))")
+    return max(X.stride(1), X.shape[0], 1)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def ghsvd_solve(h, F, J, G, n_plus: int | None = None, want_vectors: bool = True, V0=None, stream=None,
+                allow_not_converged: bool = True):
+    """Solve H z = lambda S z, H = F^* J F, S = G^* G, on device tensors.
+
+    F (m x n), G (p x n): column-major complex128 CUDA tensors.  J: int8
+    tensor of m entries +-1 (device or CPU), or None with ``n_plus`` leading
+    +1 signs (None: all +1, J = I, the GSVD).
+    Returns (lambda, V or None, sweeps, status).
+    """
+    import torch
+    m, n = F.shape
+    if n_plus is None:
+        n_plus = m
+    p = G.shape[0]
+    dev = F.device
+    lam = torch.empty(n, dtype=torch.float64, device=dev)
+    V = None
+    if want_vectors:
+        V = torch.empty_strided((n, n), (1, n), dtype=torch.complex128, device=dev)
+    Jp = None
+    if J is not None:
+        if J.dtype != torch.int8:
+            raise TypeError("J must be int8")
+        J = J.contiguous()          # keep the (possibly copied) tensor alive
+        Jp = ctypes.c_void_p(J.data_ptr())
+    sweeps = ctypes.c_int(0)
+    lib = load()
+    if V0 is None:
+        s = lib.ghsvd_solve(h, m, p, n, F.data_ptr(), ld_of(F), Jp, n_plus, G.data_ptr(), ld_of(G),
+                            lam.data_ptr(), V.data_ptr() if V is not None else None,
+                            n, ctypes.byref(sweeps), _stream_ptr(stream))
+    else:
+        s = lib.ghsvd_solve_from(h, m, p, n, F.data_ptr(), ld_of(F), Jp, n_plus, G.data_ptr(),
+                                 ld_of(G), V0.data_ptr(), ld_of(V0), lam.data_ptr(),
+                                 V.data_ptr() if V is not None else None, n,
+                                 ctypes.byref(sweeps), _stream_ptr(stream))
+    _check(s, (GHSVD_OK, GHSVD_ERR_NOT_CONVERGED) if allow_not_converged else (GHSVD_OK,))
+    return lam, V, sweeps.value, s
+
+
+def ghsvd_solve_from(h, F, J, G, V0, **kw):
+    return ghsvd_solve(h, F, J, G, V0=V0, **kw)
+
+
+def ghsvd_solve_host(h, F, J, G, n_plus: int | None = None, want_vectors: bool = True,
+                     allow_not_converged: bool = True):
+    """Host-memory variant: numpy column-major complex128 F, G; int8 J or None."""
+    import numpy as np
+    F = np.asfortranarray(F, dtype=np.complex128)
+    G = np.asfortranarray(G, dtype=np.complex128)
+    m, n = F.shape
+    if n_plus is None:
+        n_plus = m
+    p = G.shape[0]
+    lam = np.empty(n, dtype=np.float64)
+    V = np.empty((n, n), dtype=np.complex128, order="F") if want_vectors else None
+    Jp = None
+    if J is not None:
+        J = np.ascontiguousarray(J, dtype=np.int8)
+        Jp = J.ctypes.data_as(ctypes.c_void_p)
+    sweeps = ctypes.c_int(0)
+    s = load().ghsvd_solve_host(h, m, p, n, F.ctypes.data_as(ctypes.c_void_p), m, Jp, n_plus,
+                                G.ctypes.data_as(ctypes.c_void_p), p,
+                                lam.ctypes.data_as(ctypes.c_void_p),
+                                V.ctypes.data_as(ctypes.c_void_p) if V is not None else None, n,
+                                ctypes.byref(sweeps), None)
+    _check(s, (GHSVD_OK, GHSVD_ERR_NOT_CONVERGED) if allow_not_converged else (GHSVD_OK,))
+    return lam, V, sweeps.value, s
+
+
+def ghsvd_get_factors(h, m: int, p: int, n: int, device="cuda", stream=None):
+    """The transformed F' (m x n), G' (p x n) and Z' (n x n) of the last solve."""
+    import torch
+    Fp = torch.empty_strided((m, n), (1, m), dtype=torch.complex128, device=device)
+    Gp = torch.empty_strided((p, n), (1, p), dtype=torch.complex128, device=device)
+    Zp = torch.empty_strided((n, n), (1, n), dtype=torch.complex128, device=device)
+    _check(load().ghsvd_get_factors(h, Fp.data_ptr(), m, Gp.data_ptr(), p, Zp.data_ptr(), n,
+                                    _stream_ptr(stream)))
+    return Fp, Gp, Zp
+
+
+def ghsvd_get_stats(h) -> dict:
+    st = ghsvd_stats()
+    _check(load().ghsvd_get_stats(h, ctypes.byref(st)))
+    k = min(st.sweeps, 64)
+    return dict(sweeps=st.sweeps, sweeps_low=st.sweeps_low, steps_per_sweep=st.steps_per_sweep,
+                pairs_per_step=st.pairs_per_step, block_width=st.block_width,
+                transforms=list(st.transforms[:k]), big=list(st.big[:k]), ms_total=st.ms_total,
+                kernel_launches=st.kernel_launches, launches_gram=st.launches_gram,
+                launches_inner=st.launches_inner, launches_update=st.launches_update,
+                ms_gram=st.ms_gram, ms_inner=st.ms_inner, ms_update=st.ms_update)
+
+
+class Solver:
+    """Owning wrapper of a ghsvd handle."""
+
+    def __init__(self, device: int = 0, **opts):
+        self.opts = ghsvd_default_opts(**opts)
+        self.h = ghsvd_create(device, self.opts)
+
+    def solve(self, F, G, J=None, n_plus: int | None = None, **kw):
+        return ghsvd_solve(self.h, F, J, G, n_plus=n_plus, **kw)
+
+    def solve_host(self, F, G, J=None, n_plus: int | None = None, **kw):
+        return ghsvd_solve_host(self.h, F, J, G, n_plus=n_plus, **kw)
+
+    def factors(self, m, p, n, **kw):
+        return ghsvd_get_factors(self.h, m, p, n, **kw)
+
+    def stats(self):
+        return ghsvd_get_stats(self.h)
+
+    def close(self):
+        if self.h:
+            ghsvd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -334,3 +334,19 @@ def test_blocked_step_matches_block_pivot_update():
         # inner level result: Z^* S0 Z close to identity on the pivot pairs
         S3 = Zh.conj().T @ bp["S0"] @ Zh
         assert np.allclose(np.diag(S3).real, 1.0, atol=1e-8)
+
+
+def test_rank_deficient_G_is_reported():
+    # Section 6.4.2 stops on a rank-deficient pivot of S = G^* G; two equal
+    # columns of G make S singular
+    F, J, G = P.svd_pencil(31, 20, 20, 10, 4, (0.5, 2), (0.5, 2))
+    ok = oracle.solve(F, G, J)
+    assert ok["status"] == 0 and ok["kappa_est"] < 100
+    Gr = G.copy()
+    Gr[:, 3] = Gr[:, 7]
+    for method, kw in (("pointwise", {}), ("blocked", dict(w=4))):
+        assert oracle.solve(F, Gr, J, method=method, **kw)["status"] == -2
+    # the estimate tracks cond(G): C1 has cond(G) = 1e6
+    F, J, G = P.single_pencil_64()
+    k = oracle.solve(F, G, J)["kappa_est"]
+    assert 1e6 / 8 < k < 1e6 * 8
