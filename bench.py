@@ -33,7 +33,9 @@ N, M, P, M_MINUS, W_BLOCK = 2048, 3072, 4096, 512, 32
 SEED = 1907085600 + 2
 # Outer sweeps the FP64 GPU solve of this pencil takes (measured; the CPU
 # reference arm extrapolates its timed sample with it).
-SWEEPS_PER_SOLVE = 20
+SWEEPS_PER_SOLVE = 40
+# C_max: this ill-conditioned pencil needs more than the paper's ~30 sweeps
+MAX_SWEEPS = 80
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 
 
@@ -186,12 +188,14 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--max-sweeps", type=int, default=MAX_SWEEPS,
+                    help="C_max; a smaller value truncates the solve (profiling only)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -234,7 +238,8 @@ def main():
     Gd = ghsvd.colmajor(torch.from_numpy(G)).cuda()
     Jd = torch.from_numpy(J).cuda()
     prec = ghsvd.GHSVD_PRECISION_MIXED if args.precision == "mixed" else ghsvd.GHSVD_PRECISION_FP64
-    solver = ghsvd.Solver(local, block_width=W_BLOCK, precision=prec, timing=1)
+    solver = ghsvd.Solver(local, block_width=W_BLOCK, precision=prec, timing=1,
+                          max_sweeps=args.max_sweeps)
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):

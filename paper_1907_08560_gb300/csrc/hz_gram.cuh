@@ -1,0 +1,99 @@
+// hz_gram.cuh -- the block-pivot Gram kernel of one outer step (Section 6.4.2).
+#pragma once
+#include "hz_common.cuh"
+
+namespace hz {
+
+// ---------------------------------------------------------------------------
+// (a2) Block pivots, eq. 6.1 on block column pairs (Section 6.4.2):
+//   H^ = F_PQ^* J F_PQ (rows [0, m_pad)), S^ = G_PQ^* G_PQ (rows of G).
+// One CTA per (pair, row chunk); the CTA writes the kk x kk partial Gram of
+// its rows; the inner kernel sums the partials in a fixed order.
+// J enters as a sign flip of one factor (an integer xor on the sign bits).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict__ Jrow,
+            StepArgs a, typename cplx<T>::t *__restrict__ partial)
+{
+    using T2 = typename cplx<T>::t;
+    using U = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
+    __shared__ T2 xs[GRAM_KT][KKMAX];
+    __shared__ U sgn[GRAM_KT];
+    __shared__ int cols[KKMAX];
+    const int cpp = a.chunks_h + a.chunks_s;
+    const int pair = blockIdx.x / cpp;
+    const int c = blockIdx.x % cpp;
+    const bool isH = c < a.chunks_h;
+    const int r0 = isH ? c * a.kc : a.m_pad + (c - a.chunks_h) * a.kc;
+    const int r1 = isH ? min(r0 + a.kc, a.m_pad) : min(r0 + a.kc, a.m_pad + a.p_pad);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int kk = a.kk;
+    if (tid < KKMAX) cols[tid] = tid < kk ? a.slotcol[pair * kk + tid] : -1;
+    const U signbit = (U)1 << (sizeof(T) * 8 - 1);
+
+    T accr[4][4], acci[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { accr[i][j] = 0; acci[i][j] = 0; }
+
+    for (int k0 = r0; k0 < r1; k0 += GRAM_KT) {
+        __syncthreads();
+        // stage GRAM_KT rows x kk slots; consecutive threads read consecutive rows
+#pragma unroll
+        for (int q = 0; q < (GRAM_KT * KKMAX) / 256; ++q) {
+            const int e = tid + 256 * q;
+            const int r = e % GRAM_KT, s = e / GRAM_KT;
+            const int col = cols[s];
+            T2 v;
+            if (col >= 0) v = W[(long long)col * a.ld + k0 + r];
+            else { v.x = 0; v.y = 0; }
+            xs[r][s] = v;
+        }
+        if (tid < GRAM_KT) sgn[tid] = (isH && Jrow[k0 + tid] < 0) ? signbit : (U)0;
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < GRAM_KT; ++k) {
+            const U sb = sgn[k];
+            T2 x[4], y[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                x[i] = xs[k][ty + 16 * i];
+                if (sizeof(T) == 8) {
+                    x[i].x = __longlong_as_double(__double_as_longlong(x[i].x) ^ sb);
+                    x[i].y = __longlong_as_double(__double_as_longlong(x[i].y) ^ sb);
+                } else {
+                    x[i].x = __int_as_float(__float_as_int(x[i].x) ^ (unsigned)sb);
+                    x[i].y = __int_as_float(__float_as_int(x[i].y) ^ (unsigned)sb);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) y[j] = xs[k][tx + 16 * j];
+            // acc_ij += conj(J x_i) y_j
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    accr[i][j] = fma(x[i].x, y[j].x, accr[i][j]);
+                    accr[i][j] = fma(x[i].y, y[j].y, accr[i][j]);
+                    acci[i][j] = fma(x[i].x, y[j].y, acci[i][j]);
+                    acci[i][j] = fma(-x[i].y, y[j].x, acci[i][j]);
+                }
+        }
+    }
+    // partial[pair][c][i + kk j] (column-major kk x kk), only i, j < kk
+    T2 *out = partial + ((long long)pair * cpp + c) * (KKMAX * KKMAX);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int ii = ty + 16 * i, jj = tx + 16 * j;
+            T2 v;
+            v.x = accr[i][j];
+            v.y = acci[i][j];
+            out[ii + KKMAX * jj] = v;
+        }
+}
+
+}  // namespace hz

@@ -1,0 +1,85 @@
+// hz_update.cuh -- the block update of one outer step (Section 6.4.3).
+#pragma once
+#include "hz_common.cuh"
+
+namespace hz {
+
+// ---------------------------------------------------------------------------
+// (a5) Block update (Section 6.4.3): [X_P X_Q] <- [X_P X_Q] Z^ for the stacked
+// rows of F, G and Z' (the paper's three ZGEMMs).  One CTA per (64-row tile,
+// pair); pairs whose inner level applied nothing are skipped.
+// ---------------------------------------------------------------------------
+template <typename T, typename TZ>
+__global__ void __launch_bounds__(256)
+update_kernel(typename cplx<T>::t *__restrict__ W, StepArgs a,
+              const typename cplx<TZ>::t *__restrict__ zhat, const int *__restrict__ pair_flag)
+{
+    using T2 = typename cplx<T>::t;
+    extern __shared__ unsigned char smraw[];
+    T2 *zs = reinterpret_cast<T2 *>(smraw);          // [KKMAX][KKMAX] row l, col j
+    T2 *xs = zs + KKMAX * KKMAX;                      // [UPD_R][KKMAX]
+    __shared__ int cols[KKMAX];
+    const int pair = blockIdx.y;
+    if (!pair_flag[pair]) return;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int kk = a.kk;
+    const long long row0 = (long long)blockIdx.x * UPD_R;
+    if (tid < KKMAX) cols[tid] = tid < kk ? a.slotcol[pair * kk + tid] : -1;
+    const typename cplx<TZ>::t *zp = zhat + (long long)pair * KKMAX * KKMAX;
+    for (int idx = tid; idx < KKMAX * KKMAX; idx += 256) {
+        const int l = idx % KKMAX, j = idx / KKMAX;   // zhat column-major
+        T2 v;
+        if (l < kk && j < kk) { v.x = (T)zp[l + KKMAX * j].x; v.y = (T)zp[l + KKMAX * j].y; }
+        else { v.x = 0; v.y = 0; }
+        zs[l * KKMAX + j] = v;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < UPD_R * KKMAX; idx += 256) {
+        const int r = idx % UPD_R, s = idx / UPD_R;
+        const int col = cols[s];
+        T2 v;
+        if (col >= 0) v = W[(long long)col * a.ld + row0 + r];
+        else { v.x = 0; v.y = 0; }
+        xs[r * KKMAX + s] = v;
+    }
+    __syncthreads();
+    T accr[4][4], acci[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { accr[i][j] = 0; acci[i][j] = 0; }
+    for (int l = 0; l < kk; ++l) {
+        T2 x[4], z[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = xs[(ty + 16 * i) * KKMAX + l];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) z[j] = zs[l * KKMAX + tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                accr[i][j] = fma(x[i].x, z[j].x, accr[i][j]);
+                accr[i][j] = fma(-x[i].y, z[j].y, accr[i][j]);
+                acci[i][j] = fma(x[i].x, z[j].y, acci[i][j]);
+                acci[i][j] = fma(x[i].y, z[j].x, acci[i][j]);
+            }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            T2 v;
+            v.x = accr[i][j];
+            v.y = acci[i][j];
+            xs[(ty + 16 * i) * KKMAX + tx + 16 * j] = v;
+        }
+    __syncthreads();
+    for (int idx = tid; idx < UPD_R * KKMAX; idx += 256) {
+        const int r = idx % UPD_R, s = idx / UPD_R;
+        const int col = cols[s];
+        if (col >= 0) W[(long long)col * a.ld + row0 + r] = xs[r * KKMAX + s];
+    }
+}
+
+}  // namespace hz
