@@ -46,7 +46,9 @@ typedef enum {
     GHSVD_ERR_NONFINITE = 3,       /* NaN/Inf in the inputs or the iteration    */
     GHSVD_ERR_NOT_CONVERGED = 4,   /* max_sweeps reached; outputs still written */
     GHSVD_ERR_CUDA = 5,            /* a CUDA runtime error                      */
-    GHSVD_ERR_NOMEM = 6            /* device allocation failed                  */
+    GHSVD_ERR_NOMEM = 6,           /* device allocation failed                  */
+    GHSVD_ERR_SCRATCH_TOO_SMALL = 7 /* ghsvd_solve_noalloc: the problem does not
+                                      fit GHSVD_NOALLOC_SCRATCH_BYTES          */
 } ghsvd_status;
 
 /* Precision schedules. */
@@ -163,6 +165,40 @@ const char *ghsvd_status_string(ghsvd_status s);
 
 /* Release the handle and its device buffers (NULL is allowed). */
 void ghsvd_destroy(ghsvd_t h);
+
+/* Size of the device array that ghsvd_solve_noalloc works in (32 MiB). */
+#define GHSVD_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * The FP64 solve of ghsvd_solve without any device allocation.  The paper has
+ * no counterpart: it exists for callers that cannot call cudaMalloc when they
+ * solve, e.g. code running inside a host application whose memory pool has
+ * already reserved the whole device, or code that by its own rules may not
+ * allocate after start-up.
+ *
+ * All working memory (the stacked factors, Gram partials, block
+ * transformations, schedule, counters) lives in one file-scope device array
+ * of GHSVD_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads this
+ * library holds until the process exits.  No handle is needed; the call runs
+ * on the current CUDA device.  Sizes whose working set does not fit the array
+ * are rejected with GHSVD_ERR_SCRATCH_TOO_SMALL (for F 1.5n x n and G 2n x n
+ * the limit is about n = 640 at block width 32).
+ *
+ * Arguments as for ghsvd_solve, except: F, G, lambda, V and a non-NULL J must
+ * be device memory of the current device; opts (NULL: defaults) must ask for
+ * GHSVD_PRECISION_FP64; the options `timing` and `mixed_max_sweeps` are
+ * ignored.
+ *
+ * The first call on a device looks up the array's device address and sets
+ * the kernels' shared-memory limits for that device; make that first call
+ * before any stream capture.  Every call shares the array and clears the
+ * parts that must start at zero; calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be ordered by the caller.
+ */
+ghsvd_status ghsvd_solve_noalloc(int64_t m, int64_t p, int64_t n,
+                                 const void *F, int64_t ldf, const int8_t *J, int64_t n_plus,
+                                 const void *G, int64_t ldg, double *lambda, void *V, int64_t ldv,
+                                 const ghsvd_opts *opts, int *sweeps, void *stream);
 
 #ifdef __cplusplus
 }

@@ -199,6 +199,8 @@ const char *ghsvd_status_string(ghsvd_status s)
     case GHSVD_ERR_NOT_CONVERGED: return "not converged within max_sweeps";
     case GHSVD_ERR_CUDA: return "CUDA error";
     case GHSVD_ERR_NOMEM: return "out of device memory";
+    case GHSVD_ERR_SCRATCH_TOO_SMALL:
+        return "problem too large for the no-allocation scratch array (GHSVD_NOALLOC_SCRATCH_BYTES)";
     }
     return "unknown status";
 }

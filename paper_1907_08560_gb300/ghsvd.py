@@ -24,6 +24,7 @@ GHSVD_ERR_NONFINITE = 3
 GHSVD_ERR_NOT_CONVERGED = 4
 GHSVD_ERR_CUDA = 5
 GHSVD_ERR_NOMEM = 6
+GHSVD_ERR_SCRATCH_TOO_SMALL = 7
 
 GHSVD_PRECISION_FP64 = 0
 GHSVD_PRECISION_MIXED = 1
@@ -86,6 +87,9 @@ def load(path: str | None = None):
     lib.ghsvd_get_factors.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp]
     lib.ghsvd_get_stats.restype = c_int
     lib.ghsvd_get_stats.argtypes = [vp, ctypes.POINTER(ghsvd_stats)]
+    lib.ghsvd_solve_noalloc.restype = c_int
+    lib.ghsvd_solve_noalloc.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, i64,
+                                        ctypes.POINTER(ghsvd_opts), ctypes.POINTER(c_int), vp]
     lib.ghsvd_status_string.restype = ctypes.c_char_p
     lib.ghsvd_status_string.argtypes = [c_int]
     if path is None:
@@ -214,6 +218,33 @@ def ghsvd_solve_host(h, F, J, G, n_plus: int | None = None, want_vectors: bool =
                                 lam.ctypes.data_as(ctypes.c_void_p),
                                 V.ctypes.data_as(ctypes.c_void_p) if V is not None else None, n,
                                 ctypes.byref(sweeps), None)
+    _check(s, (GHSVD_OK, GHSVD_ERR_NOT_CONVERGED) if allow_not_converged else (GHSVD_OK,))
+    return lam, V, sweeps.value, s
+
+
+def ghsvd_solve_noalloc(F, J, G, n_plus: int | None = None, opts: ghsvd_opts | None = None,
+                        want_vectors: bool = True, stream=None, allow_not_converged: bool = True):
+    """The FP64 solve without device allocation inside the library (all of its
+    working memory is a fixed device array; see include/ghsvd.h).  Device
+    tensors as for ghsvd_solve; J, if given, must be a device tensor.  The
+    output tensors are allocated here by the caller's side (torch)."""
+    import torch
+    m, n = F.shape
+    if n_plus is None:
+        n_plus = m
+    p = G.shape[0]
+    lam = torch.empty(n, dtype=torch.float64, device=F.device)
+    V = torch.empty_strided((n, n), (1, n), dtype=torch.complex128, device=F.device) \
+        if want_vectors else None
+    Jp = None
+    if J is not None:
+        J = J.contiguous()
+        Jp = ctypes.c_void_p(J.data_ptr())
+    sweeps = ctypes.c_int(0)
+    s = load().ghsvd_solve_noalloc(m, p, n, F.data_ptr(), ld_of(F), Jp, n_plus, G.data_ptr(),
+                                   ld_of(G), lam.data_ptr(), V.data_ptr() if V is not None else None,
+                                   n, ctypes.byref(opts) if opts is not None else None,
+                                   ctypes.byref(sweeps), _stream_ptr(stream))
     _check(s, (GHSVD_OK, GHSVD_ERR_NOT_CONVERGED) if allow_not_converged else (GHSVD_OK,))
     return lam, V, sweeps.value, s
 
