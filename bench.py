@@ -193,6 +193,8 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--mixed-steps", type=int, default=1,
+                    help="timed solves of the mixed-precision schedule (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-sweeps", type=int, default=MAX_SWEEPS,
                     help="C_max; a smaller value truncates the solve (profiling only)")
@@ -313,6 +315,48 @@ def main():
                "h2d_bytes_per_step": (M * N + P * N) * 16 + M,
                "d2h_bytes_per_step": N * 8 + N * N * 16}
 
+    # speedup of the mixed-precision schedule over the FP64 solve at equal
+    # eigenvalue error (only alongside the default FP64 measurement)
+    mixed = None
+    if args.precision == "fp64" and args.mixed_steps > 0:
+        lam64, _, _, _ = solver.solve(Fd, Gd, Jd, stream=stream)
+        Fp64, _, _ = solver.factors(M, P, N)
+        lam64 = lam64.cpu().numpy()
+        msolver = ghsvd.Solver(local, block_width=W_BLOCK, precision=ghsvd.GHSVD_PRECISION_MIXED,
+                               max_sweeps=args.max_sweeps, mixed_max_sweeps=60)
+        msolver.solve(Fd, Gd, Jd, stream=stream)          # warm-up
+        torch.cuda.synchronize()
+        barrier()
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        mst = []
+        for _ in range(args.mixed_steps):
+            lam_m, _, sw_m, st_m = msolver.solve(Fd, Gd, Jd, stream=stream)
+            mst.append(st_m)
+        m1.record(stream)
+        torch.cuda.synchronize()
+        mixed_ms = allreduce(m0.elapsed_time(m1), dist.ReduceOp.MAX if dist else None)
+        ms_stats = msolver.stats()
+        # per-eigenvalue tolerance (cond by construction: F 1e6, G 10^5; the
+        # hyperbolic amplification a_j from the FP64 solve's converged columns)
+        F64 = Fp64.cpu().numpy()
+        Jf = J.astype(np.float64)
+        amp = (np.einsum("ij,ij->j", F64.conj(), F64).real /
+               np.abs(np.einsum("ij,i,ij->j", F64.conj(), Jf, F64).real))
+        order = np.argsort(lam64)
+        tol = 1e-12 * max(1.0, (1e6 + 10 ** 5) / 1e3) * amp[order]
+        err = np.abs(np.sort(lam_m.cpu().numpy()) - lam64[order]) / np.abs(lam64[order])
+        mvalue = world * args.mixed_steps / (mixed_ms / 1e3)
+        mixed = {"value": mvalue, "unit": "solves/s", "ms_per_step": mixed_ms / args.mixed_steps,
+                 "speedup_vs_fp64": mvalue / value, "status": mst,
+                 "sweeps_complex64": ms_stats["sweeps_low"],
+                 "sweeps_fp64": ms_stats["sweeps"] - ms_stats["sweeps_low"],
+                 "rounds_complex64": ms_stats["rounds_low"],
+                 "eig_rel_diff_vs_fp64_max": float(err.max()),
+                 "eig_rel_diff_over_tol_max": float((err / tol).max())}
+        msolver.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(F, G, J, round(sweeps_per_solve))
@@ -328,7 +372,7 @@ def main():
                            "precision": args.precision, "sweeps_per_solve": sweeps_per_solve,
                            "status": status, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (235 MB)"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed_precision": mixed,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -53,10 +53,11 @@ typedef enum {
 
 /* Precision schedules. */
 #define GHSVD_PRECISION_FP64 0     /* every sweep in complex128 / FP64            */
-#define GHSVD_PRECISION_MIXED 1    /* complex64 preconditioning sweeps with FP32
-                                      accumulation, then FP64 finishing sweeps;
-                                      the 2x2 parameters, J-norms and the
-                                      stopping test are always FP64            */
+#define GHSVD_PRECISION_MIXED 1    /* rounds of complex64 preconditioning sweeps
+                                      with FP32 accumulation, each applied to the
+                                      FP64 factors by an FP64 product, then FP64
+                                      finishing sweeps; the 2x2 parameters,
+                                      J-norms and the stopping test are FP64  */
 
 typedef struct {
     int block_width;     /* w: maximal block-column width, 1..32 (Section 6.4.1);
@@ -90,6 +91,7 @@ typedef struct {
     long long kernel_launches;     /* kernels this library launched in the solve */
     long long launches_gram, launches_inner, launches_update;
     double ms_gram, ms_inner, ms_update;   /* summed device time (timing = 1)     */
+    int rounds_low;                /* complex64 rounds (mixed schedule)          */
 } ghsvd_stats;
 
 /* Fill *opts with the defaults listed above. */

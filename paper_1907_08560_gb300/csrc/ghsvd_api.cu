@@ -391,7 +391,7 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
 
     h->m = m; h->p = p; h->n = n; h->m_pad = m_pad; h->p_pad = p_pad; h->n_pad = n_pad; h->Mt = Mt;
     ghsvd_status status = GHSVD_ERR_NOT_CONVERGED;
-    int sweeps = 0, sweeps_low = 0;
+    int sweeps = 0, sweeps_low = 0, rounds = 0;
     h->stats.steps_per_sweep = nsteps;
     h->stats.pairs_per_step = npairs;
     h->stats.block_width = wb;
@@ -410,10 +410,18 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
         // so that pivots below the Gram's rounding level are left alone
         const double tol32 = ldexp(1.0, -24) * sqrt((double)n);
 
-        // mixed schedule: complex64 preconditioning sweeps on a copy of
-        // (F, G) with Z' restarted at I; their Z' is then applied to the FP64
-        // factors (W <- W Z'_low) and FP64 sweeps finish the iteration
+        // Mixed schedule (iterative refinement): complex64 sweeps run on
+        // W32 = fl32(W) with Z' restarted at I until their big transformations
+        // stagnate at the complex64 rounding level; the accumulated Z'_low is
+        // then applied to the FP64 factors, W <- W Z'_low (an exact congruence
+        // of the pencil, in FP64), and, while a round still made progress, a
+        // new complex64 round starts from fl32 of the improved W, whose columns
+        // are now nearly orthogonal so that rounding them to complex64 no
+        // longer perturbs the ill-conditioned directions.  FP64 sweeps finish.
         int phase_single = mixed ? 1 : 0;
+        int round_sweeps = 0;
+        unsigned long long prev_big = ~0ULL;
+        const double pivots_per_sweep = (double)nsteps * npairs * (kk / 2) * (kk - 1);
         if (mixed) {
             CUDA_TRY(hz::launch_convert(h->W32, true, h->W, Mt * n, st));
             CUDA_TRY(hz::launch_eye32(h->W32, Mt, m_pad + p_pad, n, n_pad, st));
@@ -469,17 +477,30 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
             if (h->h_err[0] & hz::DEVERR_RANK) { status = GHSVD_ERR_RANK_DEFICIENT; break; }
             if (h->h_err[0] & hz::DEVERR_NONFINITE) { status = GHSVD_ERR_NONFINITE; break; }
             if (single) {
-                // leave the complex64 phase once it stops making big progress
-                // or its sweep budget is spent; the FP64 phase restarts from
-                // the original F, G transformed by the accumulated Z'
-                const bool done = h->h_counters[0] == 0 || sweeps_low >= o.mixed_max_sweeps;
-                if (done) {
-                    phase_single = 0;
+                ++round_sweeps;
+                const unsigned long long all = h->h_counters[0], big = h->h_counters[1];
+                // stagnation: fewer than 1 % of the pivots still rotate "big"
+                // and that number no longer falls by a fifth per sweep
+                const bool plateau = round_sweeps >= 2 && (double)big > 0.8 * (double)prev_big &&
+                                     (double)big < 0.01 * pivots_per_sweep;
+                prev_big = big;
+                const bool budget = sweeps_low >= o.mixed_max_sweeps;
+                if (all == 0 || plateau || budget) {
                     const float2 *zlow = h->W32 + (m_pad + p_pad);
                     CUDA_TRY(hz::launch_gemm(h->W, Mt, (int)Mt, zlow, true, Mt, h->Wtmp, Mt, n, st));
-                    h->stats.kernel_launches += 1;
                     CUDA_TRY(cudaMemcpyAsync(h->W, h->Wtmp, sizeof(double2) * Mt * n,
                                              cudaMemcpyDeviceToDevice, st));
+                    h->stats.kernel_launches += 1;
+                    ++rounds;
+                    if (budget || all == 0 || round_sweeps <= 3 || rounds >= 4) {
+                        phase_single = 0;            // FP64 finishing sweeps
+                    } else {                         // next complex64 round
+                        CUDA_TRY(hz::launch_convert(h->W32, true, h->W, Mt * n, st));
+                        CUDA_TRY(hz::launch_eye32(h->W32, Mt, m_pad + p_pad, n, n_pad, st));
+                        h->stats.kernel_launches += 2;
+                        round_sweeps = 0;
+                        prev_big = ~0ULL;
+                    }
                 }
                 continue;
             }
@@ -488,6 +509,7 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
     }
     h->stats.sweeps = sweeps;
     h->stats.sweeps_low = sweeps_low;
+    h->stats.rounds_low = rounds;
     if (status == GHSVD_ERR_RANK_DEFICIENT || status == GHSVD_ERR_NONFINITE) return status;
 
     // outputs (Section 6.1.7)

@@ -7,12 +7,17 @@ namespace hz {
 // ---------------------------------------------------------------------------
 // (a2) Block pivots, eq. 6.1 on block column pairs (Section 6.4.2):
 //   H^ = F_PQ^* J F_PQ (rows [0, m_pad)), S^ = G_PQ^* G_PQ (rows of G).
-// One CTA per (pair, row chunk); the CTA writes the kk x kk partial Gram of
-// its rows; the inner kernel sums the partials in a fixed order.
-// J enters as a sign flip of one factor (an integer xor on the sign bits).
+// One CTA per (pair, row chunk); the CTA writes the partial Gram of its rows;
+// the inner kernel sums the partials in a fixed order.
+//
+// The block pivots are Hermitian, so only the two diagonal 32 x 32 quadrants
+// and the upper off-diagonal one are computed (3 of 4; 1 when kk <= 32).
+// 64 threads per quadrant, each a 4 x 4 tile of complex outputs (rows
+// q_r + ty + 8i, columns q_c + tx + 8j).  J enters as a sign flip of the
+// conjugated factor (an integer xor on the sign bits).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(192)
 gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict__ Jrow,
             StepArgs a, typename cplx<T>::t *__restrict__ partial)
 {
@@ -27,9 +32,12 @@ gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict_
     const bool isH = c < a.chunks_h;
     const int r0 = isH ? c * a.kc : a.m_pad + (c - a.chunks_h) * a.kc;
     const int r1 = isH ? min(r0 + a.kc, a.m_pad) : min(r0 + a.kc, a.m_pad + a.p_pad);
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int quad = tid >> 6, t = tid & 63, tx = t & 7, ty = t >> 3;
+    // quadrant 0: (0,0), 1: (0,1), 2: (1,1), in units of 32
+    const int qr = quad == 2 ? 32 : 0, qc = quad == 0 ? 0 : 32;
     const int kk = a.kk;
-    if (tid < KKMAX) cols[tid] = tid < kk ? a.slotcol[pair * kk + tid] : -1;
+    for (int s = tid; s < KKMAX; s += nthr) cols[s] = s < kk ? a.slotcol[pair * kk + s] : -1;
     const U signbit = (U)1 << (sizeof(T) * 8 - 1);
 
     T accr[4][4], acci[4][4];
@@ -40,10 +48,8 @@ gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict_
 
     for (int k0 = r0; k0 < r1; k0 += GRAM_KT) {
         __syncthreads();
-        // stage GRAM_KT rows x kk slots; consecutive threads read consecutive rows
-#pragma unroll
-        for (int q = 0; q < (GRAM_KT * KKMAX) / 256; ++q) {
-            const int e = tid + 256 * q;
+        // stage GRAM_KT rows x KKMAX slots; consecutive threads read consecutive rows
+        for (int e = tid; e < GRAM_KT * KKMAX; e += nthr) {
             const int r = e % GRAM_KT, s = e / GRAM_KT;
             const int col = cols[s];
             T2 v;
@@ -59,7 +65,7 @@ gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict_
             T2 x[4], y[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                x[i] = xs[k][ty + 16 * i];
+                x[i] = xs[k][qr + ty + 8 * i];
                 if (sizeof(T) == 8) {
                     x[i].x = __longlong_as_double(__double_as_longlong(x[i].x) ^ sb);
                     x[i].y = __longlong_as_double(__double_as_longlong(x[i].y) ^ sb);
@@ -69,7 +75,7 @@ gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict_
                 }
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) y[j] = xs[k][tx + 16 * j];
+            for (int j = 0; j < 4; ++j) y[j] = xs[k][qc + tx + 8 * j];
             // acc_ij += conj(J x_i) y_j
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -82,13 +88,13 @@ gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict_
                 }
         }
     }
-    // partial[pair][c][i + kk j] (column-major kk x kk), only i, j < kk
+    // partial[pair][c][i + KKMAX j] (column-major), computed quadrants only
     T2 *out = partial + ((long long)pair * cpp + c) * (KKMAX * KKMAX);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int ii = ty + 16 * i, jj = tx + 16 * j;
+            const int ii = qr + ty + 8 * i, jj = qc + tx + 8 * j;
             T2 v;
             v.x = accr[i][j];
             v.y = acci[i][j];

@@ -4,6 +4,38 @@
 
 namespace hz {
 
+// Complex helpers for the shared-memory block pivots (T = double or float).
+template <typename T2, typename T>
+__device__ __forceinline__ T2 c_make(T x, T y)
+{
+    T2 r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+
+// [x0 x1] <- [x0 x1] Z, Z = {z11, z12; z21, z22} given as z[0..7] (re, im).
+template <typename T2, typename T>
+__device__ __forceinline__ void c_right(T2 &x0, T2 &x1, const T *z)
+{
+    const T2 a = x0, b = x1;
+    x0.x = a.x * z[0] - a.y * z[1] + b.x * z[4] - b.y * z[5];
+    x0.y = a.x * z[1] + a.y * z[0] + b.x * z[5] + b.y * z[4];
+    x1.x = a.x * z[2] - a.y * z[3] + b.x * z[6] - b.y * z[7];
+    x1.y = a.x * z[3] + a.y * z[2] + b.x * z[7] + b.y * z[6];
+}
+
+// [x0; x1] <- Z^* [x0; x1] (Z^* = {conj z11, conj z21; conj z12, conj z22}).
+template <typename T2, typename T>
+__device__ __forceinline__ void c_left(T2 &x0, T2 &x1, const T *z)
+{
+    const T2 a = x0, b = x1;
+    x0.x = z[0] * a.x + z[1] * a.y + z[4] * b.x + z[5] * b.y;
+    x0.y = z[0] * a.y - z[1] * a.x + z[4] * b.y - z[5] * b.x;
+    x1.x = z[2] * a.x + z[3] * a.y + z[6] * b.x + z[7] * b.y;
+    x1.y = z[2] * a.y - z[3] * a.x + z[6] * b.y - z[7] * b.x;
+}
+
 // ---------------------------------------------------------------------------
 // (a3, a4) The inner level on one block pivot (Section 6.4.2): sum the Gram
 // partials, then run `inner_sweeps` sweeps of the pointwise method on the
@@ -13,23 +45,34 @@ namespace hz {
 // with Z_all the block-diagonal product of the step's 2x2 transformations,
 // each 2x2 block (I, J) of H^ becomes Z_I^* H^_IJ Z_J; only I <= J is
 // computed, the mirror block is its conjugate transpose.
+//
+// TP is the type of the Gram partials, TU the type in which the block
+// pivots are kept and transformed (double for the FP64 sweeps, float for the
+// complex64 preconditioning sweeps).  The 2x2 parameters (eq. 6.5-6.12) are
+// always computed in FP64 from the pivot entries.
+//
+// The Gram kernel writes the two diagonal 32 x 32 quadrants and the upper
+// off-diagonal one; the lower off-diagonal quadrant is the conjugate
+// transpose of the upper one (the block pivots are Hermitian).
 // One CTA (1024 threads) per block pivot; H^, S^, Z^ live in shared memory.
 // ---------------------------------------------------------------------------
-template <typename TP>   // type of the Gram partials (double or float)
+template <typename TP, typename TU>
 __global__ void __launch_bounds__(1024)
 inner_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__restrict__ slotcol,
              InnerArgs a, double2 *__restrict__ zhat, int *__restrict__ pair_flag,
              unsigned long long *__restrict__ counters, int *__restrict__ err)
 {
-    extern __shared__ double2 smem[];
-    double2 *H = smem;                       // [KKMAX * KKMAX], column-major
-    double2 *S = H + KKMAX * KKMAX;
-    double2 *Z = S + KKMAX * KKMAX;
-    __shared__ double zp[KKMAX / 2][8];      // the step's 2x2 transformations
+    using U2 = typename cplx<TU>::t;
+    extern __shared__ unsigned char smraw_inner[];
+    U2 *H = reinterpret_cast<U2 *>(smraw_inner);   // [kk * kk], column-major
+    U2 *S = H + KKMAX * KKMAX;
+    U2 *Z = S + KKMAX * KKMAX;
+    __shared__ double zp[KKMAX / 2][8];      // the step's 2x2 transformations (FP64)
+    __shared__ TU zu[KKMAX / 2][8];          // the same in the update type
     __shared__ int tr[KKMAX / 2];            // pivot transformed?
     __shared__ int pslot[KKMAX];             // slots of pivot l: 2l, 2l+1
     __shared__ int valid[KKMAX];
-    __shared__ int s_all, s_big, s_err;
+    __shared__ int s_all, s_big, s_err, s_sweep;
     const int pair = blockIdx.x;
     const int tid = threadIdx.x;
     const int kk = a.kk, np = kk / 2;
@@ -37,11 +80,12 @@ inner_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__rest
     if (tid == 0) { s_all = 0; s_big = 0; s_err = 0; }
     __syncthreads();
 
-    // sum the partial Grams in chunk order (deterministic)
+    // sum the partial Grams in chunk order (deterministic, in FP64)
     const typename cplx<TP>::t *pp = partial + (long long)pair * a.cpp * (KKMAX * KKMAX);
     for (int idx = tid; idx < kk * kk; idx += blockDim.x) {
         const int i = idx % kk, j = idx / kk;
-        const int e = i + KKMAX * j;
+        const bool mirror = i >= KKMAX / 2 && j < KKMAX / 2;   // lower off-diagonal quadrant
+        const int e = mirror ? j + KKMAX * i : i + KKMAX * j;
         double hr = 0, hi = 0, sr = 0, si = 0;
         for (int c = 0; c < a.chunks_h; ++c) {
             hr += (double)pp[(long long)c * KKMAX * KKMAX + e].x;
@@ -51,18 +95,18 @@ inner_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__rest
             sr += (double)pp[(long long)c * KKMAX * KKMAX + e].x;
             si += (double)pp[(long long)c * KKMAX * KKMAX + e].y;
         }
+        if (mirror) { hi = -hi; si = -si; }
         if (i == j) {          // Hermitian: real diagonal; bordered slot: S = 1
             hi = 0; si = 0;
             if (!valid[i]) { sr = 1.0; hr = 0.0; }
         }
-        H[i + kk * j] = make_double2(hr, hi);
-        S[i + kk * j] = make_double2(sr, si);
-        Z[i + kk * j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+        H[i + kk * j] = c_make<U2, TU>((TU)hr, (TU)hi);
+        S[i + kk * j] = c_make<U2, TU>((TU)sr, (TU)si);
+        Z[i + kk * j] = c_make<U2, TU>((TU)(i == j ? 1 : 0), (TU)0);
     }
     __syncthreads();
 
     int my_all = 0, my_big = 0;
-    __shared__ int s_sweep;
     for (int isw = 0; isw < a.inner_sweeps; ++isw) {
         if (tid == 0) s_sweep = 0;
         __syncthreads();
@@ -78,9 +122,10 @@ inner_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__rest
                     pslot[2 * l + 1] = pb;
                     int rc = PIV_NONE, big = 0;
                     if (valid[pa] && valid[pb]) {
-                        const double2 hab = H[pa + kk * pb], sab = S[pa + kk * pb];
-                        rc = pivot2x2(H[pa + kk * pa].x, H[pb + kk * pb].x, hab.x, hab.y,
-                                      S[pa + kk * pa].x, S[pb + kk * pb].x, sab.x, sab.y,
+                        const U2 hab = H[pa + kk * pb], sab = S[pa + kk * pb];
+                        rc = pivot2x2((double)H[pa + kk * pa].x, (double)H[pb + kk * pb].x,
+                                      (double)hab.x, (double)hab.y, (double)S[pa + kk * pa].x,
+                                      (double)S[pb + kk * pb].x, (double)sab.x, (double)sab.y,
                                       a.tol, a.crit_mode, zp[l], &big);
                     }
                     if (rc < 0) {
@@ -88,7 +133,13 @@ inner_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__rest
                         rc = PIV_NONE;
                     }
                     tr[l] = rc == PIV_TRANSFORM;
-                    if (rc == PIV_TRANSFORM) { my_all += 1; my_big += big; step_all += 1; }
+                    if (rc == PIV_TRANSFORM) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) zu[l][q] = (TU)zp[l][q];
+                        my_all += 1;
+                        my_big += big;
+                        step_all += 1;
+                    }
                 }
                 if (step_all) atomicAdd(&s_sweep, step_all);
             }
@@ -105,67 +156,47 @@ inner_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__rest
                     while (b >= np - I) { b -= np - I; ++I; }
                     const int Jb = I + b;
                     if (!tr[I] && !tr[Jb]) continue;
-                    double2 *A = mat ? S : H;
+                    U2 *A = mat ? S : H;
                     const int aI = pslot[2 * I], bI = pslot[2 * I + 1];
                     const int aJ = pslot[2 * Jb], bJ = pslot[2 * Jb + 1];
-                    double2 x00 = A[aI + kk * aJ], x01 = A[aI + kk * bJ];
-                    double2 x10 = A[bI + kk * aJ], x11 = A[bI + kk * bJ];
-                    if (tr[Jb]) {            // right: [x] <- [x] Z_J
-                        const double *z = zp[Jb];
-                        double2 y00, y01, y10, y11;
-                        y00.x = x00.x * z[0] - x00.y * z[1] + x01.x * z[4] - x01.y * z[5];
-                        y00.y = x00.x * z[1] + x00.y * z[0] + x01.x * z[5] + x01.y * z[4];
-                        y01.x = x00.x * z[2] - x00.y * z[3] + x01.x * z[6] - x01.y * z[7];
-                        y01.y = x00.x * z[3] + x00.y * z[2] + x01.x * z[7] + x01.y * z[6];
-                        y10.x = x10.x * z[0] - x10.y * z[1] + x11.x * z[4] - x11.y * z[5];
-                        y10.y = x10.x * z[1] + x10.y * z[0] + x11.x * z[5] + x11.y * z[4];
-                        y11.x = x10.x * z[2] - x10.y * z[3] + x11.x * z[6] - x11.y * z[7];
-                        y11.y = x10.x * z[3] + x10.y * z[2] + x11.x * z[7] + x11.y * z[6];
-                        x00 = y00; x01 = y01; x10 = y10; x11 = y11;
+                    U2 x00 = A[aI + kk * aJ], x01 = A[aI + kk * bJ];
+                    U2 x10 = A[bI + kk * aJ], x11 = A[bI + kk * bJ];
+                    if (tr[Jb]) {            // right: rows of the block times Z_J
+                        c_right<U2, TU>(x00, x01, zu[Jb]);
+                        c_right<U2, TU>(x10, x11, zu[Jb]);
                     }
-                    if (tr[I]) {             // left: [x] <- Z_I^* [x]
-                        const double *z = zp[I];
-                        // Z^* = [conj z11, conj z21; conj z12, conj z22]
-                        double2 y00, y01, y10, y11;
-                        y00.x = z[0] * x00.x + z[1] * x00.y + z[4] * x10.x + z[5] * x10.y;
-                        y00.y = z[0] * x00.y - z[1] * x00.x + z[4] * x10.y - z[5] * x10.x;
-                        y01.x = z[0] * x01.x + z[1] * x01.y + z[4] * x11.x + z[5] * x11.y;
-                        y01.y = z[0] * x01.y - z[1] * x01.x + z[4] * x11.y - z[5] * x11.x;
-                        y10.x = z[2] * x00.x + z[3] * x00.y + z[6] * x10.x + z[7] * x10.y;
-                        y10.y = z[2] * x00.y - z[3] * x00.x + z[6] * x10.y - z[7] * x10.x;
-                        y11.x = z[2] * x01.x + z[3] * x01.y + z[6] * x11.x + z[7] * x11.y;
-                        y11.y = z[2] * x01.y - z[3] * x01.x + z[6] * x11.y - z[7] * x11.x;
-                        x00 = y00; x01 = y01; x10 = y10; x11 = y11;
+                    if (tr[I]) {             // left: Z_I^* times columns of the block
+                        c_left<U2, TU>(x00, x10, zu[I]);
+                        c_left<U2, TU>(x01, x11, zu[I]);
                     }
-                    if (I == Jb) { x00.y = 0.0; x11.y = 0.0; x10 = make_double2(x01.x, -x01.y); }
+                    if (I == Jb) {
+                        x00.y = 0;
+                        x11.y = 0;
+                        x10 = c_make<U2, TU>(x01.x, -x01.y);
+                    }
                     A[aI + kk * aJ] = x00; A[aI + kk * bJ] = x01;
                     A[bI + kk * aJ] = x10; A[bI + kk * bJ] = x11;
                     if (I != Jb) {
-                        A[aJ + kk * aI] = make_double2(x00.x, -x00.y);
-                        A[bJ + kk * aI] = make_double2(x01.x, -x01.y);
-                        A[aJ + kk * bI] = make_double2(x10.x, -x10.y);
-                        A[bJ + kk * bI] = make_double2(x11.x, -x11.y);
+                        A[aJ + kk * aI] = c_make<U2, TU>(x00.x, -x00.y);
+                        A[bJ + kk * aI] = c_make<U2, TU>(x01.x, -x01.y);
+                        A[aJ + kk * bI] = c_make<U2, TU>(x10.x, -x10.y);
+                        A[bJ + kk * bI] = c_make<U2, TU>(x11.x, -x11.y);
                     }
                 } else {
                     const int q = it - 2 * nblk;
                     const int row = q % kk, l = q / kk;
                     if (!tr[l]) continue;
-                    const double *z = zp[l];
                     const int pa = pslot[2 * l], pb = pslot[2 * l + 1];
-                    const double2 u = Z[row + kk * pa], w = Z[row + kk * pb];
-                    double2 ya, yb;
-                    ya.x = u.x * z[0] - u.y * z[1] + w.x * z[4] - w.y * z[5];
-                    ya.y = u.x * z[1] + u.y * z[0] + w.x * z[5] + w.y * z[4];
-                    yb.x = u.x * z[2] - u.y * z[3] + w.x * z[6] - w.y * z[7];
-                    yb.y = u.x * z[3] + u.y * z[2] + w.x * z[7] + w.y * z[6];
-                    Z[row + kk * pa] = ya;
-                    Z[row + kk * pb] = yb;
+                    U2 u = Z[row + kk * pa], w = Z[row + kk * pb];
+                    c_right<U2, TU>(u, w, zu[l]);
+                    Z[row + kk * pa] = u;
+                    Z[row + kk * pb] = w;
                 }
             }
             __syncthreads();
         }
         // FB: stop after an inner sweep without any transformation
-        // (Section 6.1.7: the inner levels count all transformations)
+        // (Section 6.1.7, the inner levels count all transformations)
         const int swept = s_sweep;
         __syncthreads();
         if (swept == 0) break;
@@ -173,11 +204,12 @@ inner_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__rest
     if (my_all) atomicAdd(&s_all, my_all);
     if (my_big) atomicAdd(&s_big, my_big);
     __syncthreads();
-    // Zhat[pair] (kk x kk, column-major, ld KKMAX)
+    // Zhat[pair] (kk x kk, column-major, ld KKMAX), FP64
     double2 *zo = zhat + (long long)pair * KKMAX * KKMAX;
     for (int idx = tid; idx < kk * kk; idx += blockDim.x) {
         const int i = idx % kk, j = idx / kk;
-        zo[i + KKMAX * j] = Z[i + kk * j];
+        const U2 v = Z[i + kk * j];
+        zo[i + KKMAX * j] = make_double2((double)v.x, (double)v.y);
     }
     if (tid == 0) {
         pair_flag[pair] = s_all > 0;

@@ -339,23 +339,27 @@ cudaError_t launch_gram(const void *W, bool single, const int8_t *Jrow, const St
                         void *partial, cudaStream_t s)
 {
     const int grid = a.npairs * (a.chunks_h + a.chunks_s);
+    const int threads = a.kk > KKMAX / 2 ? 192 : 64;   // 3 quadrants, or 1
     if (single)
-        gram_kernel<float><<<grid, 256, 0, s>>>((const float2 *)W, Jrow, a, (float2 *)partial);
+        gram_kernel<float><<<grid, threads, 0, s>>>((const float2 *)W, Jrow, a, (float2 *)partial);
     else
-        gram_kernel<double><<<grid, 256, 0, s>>>((const double2 *)W, Jrow, a, (double2 *)partial);
+        gram_kernel<double><<<grid, threads, 0, s>>>((const double2 *)W, Jrow, a, (double2 *)partial);
     return cudaGetLastError();
 }
 
-static size_t inner_smem() { return 3 * sizeof(double2) * KKMAX * KKMAX; }
+static size_t inner_smem(bool single)
+{
+    return 3 * (single ? sizeof(float2) : sizeof(double2)) * KKMAX * KKMAX;
+}
 
 cudaError_t setup_kernels()
 {
     cudaError_t e;
-    e = cudaFuncSetAttribute(inner_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)inner_smem());
+    e = cudaFuncSetAttribute(inner_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)inner_smem(false));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(inner_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)inner_smem());
+    e = cudaFuncSetAttribute(inner_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)inner_smem(true));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(update_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(2 * sizeof(double2) * KKMAX * KKMAX));
@@ -370,11 +374,11 @@ cudaError_t launch_inner(const void *partial, bool single, const int *slotcol, c
                          cudaStream_t s)
 {
     if (single)
-        inner_kernel<float><<<a.npairs, 1024, inner_smem(), s>>>((const float2 *)partial, slotcol, a,
-                                                                zhat, pair_flag, counters, err);
+        inner_kernel<float, float><<<a.npairs, 1024, inner_smem(true), s>>>(
+            (const float2 *)partial, slotcol, a, zhat, pair_flag, counters, err);
     else
-        inner_kernel<double><<<a.npairs, 1024, inner_smem(), s>>>((const double2 *)partial, slotcol, a,
-                                                                 zhat, pair_flag, counters, err);
+        inner_kernel<double, double><<<a.npairs, 1024, inner_smem(false), s>>>(
+            (const double2 *)partial, slotcol, a, zhat, pair_flag, counters, err);
     return cudaGetLastError();
 }
 

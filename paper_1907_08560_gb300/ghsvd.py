@@ -46,7 +46,8 @@ class ghsvd_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
                 ("launches_gram", ctypes.c_longlong), ("launches_inner", ctypes.c_longlong),
                 ("launches_update", ctypes.c_longlong), ("ms_gram", ctypes.c_double),
-                ("ms_inner", ctypes.c_double), ("ms_update", ctypes.c_double)]
+                ("ms_inner", ctypes.c_double), ("ms_update", ctypes.c_double),
+                ("rounds_low", ctypes.c_int)]
 
 
 class GhsvdError(RuntimeError):
@@ -269,7 +270,8 @@ def ghsvd_get_stats(h) -> dict:
                 transforms=list(st.transforms[:k]), big=list(st.big[:k]), ms_total=st.ms_total,
                 kernel_launches=st.kernel_launches, launches_gram=st.launches_gram,
                 launches_inner=st.launches_inner, launches_update=st.launches_update,
-                ms_gram=st.ms_gram, ms_inner=st.ms_inner, ms_update=st.ms_update)
+                ms_gram=st.ms_gram, ms_inner=st.ms_inner, ms_update=st.ms_update,
+                rounds_low=st.rounds_low)
 
 
 class Solver:
