@@ -61,7 +61,8 @@ typedef enum {
 
 typedef struct {
     int block_width;     /* w: maximal block-column width, 1..32 (Section 6.4.1);
-                            default 32                                        */
+                            default 32; 0: automatic (32 for one pencil, the
+                            autotuner for ghsvd_solve_batched)                */
     int inner_sweeps;    /* inner sweeps per block pivot: 1 = BO (default),
                             up to 30 = FB (Section 6.4.2)                     */
     int max_sweeps;      /* C_max for the outer (block) sweeps, default 30
@@ -167,6 +168,38 @@ const char *ghsvd_status_string(ghsvd_status s);
 
 /* Release the handle and its device buffers (NULL is allowed). */
 void ghsvd_destroy(ghsvd_t h);
+
+/*
+ * Batched solves: `batch` independent pencils (F_i, J_i, G_i) of uneven
+ * orders, e.g. the k-points of one LAPW computation.  Every pencil follows
+ * its own block schedule (Section 6.4.1, 6.3) and stopping rule (no big
+ * transformation in its sweep, Section 6.1.7); one outer step of every
+ * pencil that has not stopped runs per "tick" (a Gram, an inner and an
+ * update kernel over all pencils, and a control kernel on the device), and
+ * the ticks are replayed as a CUDA graph until every pencil has stopped.
+ *   m, p, n       host arrays [batch]: sizes of pencil i (n_i >= 2).
+ *   F, G          host arrays [batch] of device pointers (complex128,
+ *                 column-major) with host arrays ldf, ldg [batch].
+ *   J             host array [batch] of device int8 pointers (+-1 each), or
+ *                 NULL; a NULL array or entry means positives first with
+ *                 n_plus[i] leading +1 signs (n_plus NULL: J = I).
+ *   lambda        host array [batch] of device pointers (n_i doubles each).
+ *   V, ldv        host arrays [batch] of device pointers and leading
+ *                 dimensions, or NULL V (no eigenvectors).
+ *   sweeps, status  host arrays [batch] (may be NULL): sweeps run and the
+ *                 status of every pencil.
+ * The handle's block_width is used for every pencil; block_width = 0 picks
+ * it from {8, 16, 32} by timing a few ticks of each (the autotuner); the
+ * choice is reported in ghsvd_stats.block_width.  FP64 schedule only.
+ * Returns GHSVD_OK when every pencil converged, otherwise the status of the
+ * first pencil that failed (or GHSVD_ERR_NOT_CONVERGED).
+ */
+ghsvd_status ghsvd_solve_batched(ghsvd_t h, int batch, const int64_t *m, const int64_t *p,
+                                 const int64_t *n, const void *const *F, const int64_t *ldf,
+                                 const int8_t *const *J, const int64_t *n_plus,
+                                 const void *const *G, const int64_t *ldg, double *const *lambda,
+                                 void *const *V, const int64_t *ldv, int *sweeps, int *status,
+                                 void *stream);
 
 /* Size of the device array that ghsvd_solve_noalloc works in (32 MiB). */
 #define GHSVD_NOALLOC_SCRATCH_BYTES (32u << 20)

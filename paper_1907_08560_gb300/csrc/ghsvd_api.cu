@@ -75,6 +75,7 @@ struct ghsvd_ctx {
     bool solved = false;
     ghsvd_stats stats{};
     KTimer timer;
+    void *batch = nullptr;              // working memory of ghsvd_solve_batched
 };
 
 // ---------------------------------------------------------------------------
@@ -110,6 +111,8 @@ static cudaError_t grow(T **ptr, long long count, long long *cap)
 static void free_all(ghsvd_ctx *h)
 {
     h->timer.release();
+    hz_batch_free(h->batch);
+    h->batch = nullptr;
     cudaFree(h->W); cudaFree(h->W32); cudaFree(h->Wtmp); cudaFree(h->partial); cudaFree(h->zhat);
     cudaFree(h->pair_flag); cudaFree(h->slotcol); cudaFree(h->Jrow); cudaFree(h->Jdev);
     cudaFree(h->counters); cudaFree(h->err); cudaFree(h->lam_tmp); cudaFree(h->gscale);
@@ -212,7 +215,7 @@ ghsvd_status ghsvd_create(ghsvd_t *out, int device, const ghsvd_opts *opts)
     ghsvd_opts o;
     if (opts) o = *opts;
     else ghsvd_default_opts(&o);
-    if (o.block_width < 1 || o.block_width > hz::KKMAX / 2 || o.inner_sweeps < 1 ||
+    if (o.block_width < 0 || o.block_width > hz::KKMAX / 2 || o.inner_sweeps < 1 ||
         o.inner_sweeps > 30 || o.max_sweeps < 1 || o.max_sweeps > 1000 ||
         (o.crit_mode != 0 && o.crit_mode != 1) ||
         (o.precision != GHSVD_PRECISION_FP64 && o.precision != GHSVD_PRECISION_MIXED) ||
@@ -284,7 +287,8 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
     std::vector<int> off;
     int nb = 0, wb = 1, kk = 2, npairs = 0, nsteps = 0;
     if (n >= 2) {
-        nb = partition(n, std::min(o.block_width, n), off);
+        const int w = o.block_width > 0 ? o.block_width : 32;   // 0: automatic (32 for one pencil)
+        nb = partition(n, std::min(w, n), off);
         wb = off[1] - off[0];
         kk = 2 * wb;
         npairs = nb / 2;
@@ -639,3 +643,41 @@ ghsvd_status ghsvd_get_factors(ghsvd_t h, void *Fp, int64_t ldf, void *Gp, int64
 }
 
 }  // extern "C"
+
+extern "C" ghsvd_status ghsvd_solve_batched(ghsvd_t h, int batch, const int64_t *m, const int64_t *p,
+                                           const int64_t *n, const void *const *F, const int64_t *ldf,
+                                           const int8_t *const *J, const int64_t *n_plus,
+                                           const void *const *G, const int64_t *ldg,
+                                           double *const *lambda, void *const *V, const int64_t *ldv,
+                                           int *sweeps, int *status, void *stream)
+{
+    if (!h || batch < 1 || !m || !p || !n || !F || !ldf || !G || !ldg || !lambda)
+        return GHSVD_ERR_INVALID_ARG;
+    if (h->opts.precision != GHSVD_PRECISION_FP64) return GHSVD_ERR_INVALID_ARG;
+    for (int i = 0; i < batch; ++i) {
+        const int8_t *Ji = J ? J[i] : nullptr;
+        const int64_t np_ = n_plus ? n_plus[i] : m[i];
+        ghsvd_status s = validate(h, m[i], p[i], n[i], F[i], ldf[i], Ji, np_, G[i], ldg[i], lambda[i],
+                                  V ? V[i] : nullptr, ldv ? ldv[i] : n[i]);
+        if (s != GHSVD_OK) return s;
+        if (n[i] < 2 || n[i] > (1 << 20)) return GHSVD_ERR_INVALID_ARG;
+        if (!is_device_ptr(F[i]) || !is_device_ptr(G[i]) || !is_device_ptr(lambda[i]) ||
+            (V && V[i] && !is_device_ptr(V[i])) || (Ji && !is_device_ptr(Ji)))
+            return GHSVD_ERR_INVALID_ARG;
+    }
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(h->device) != cudaSuccess) return GHSVD_ERR_CUDA;
+    if (!h->batch) h->batch = hz_batch_new();
+    if (!h->batch) { cudaSetDevice(prev); return GHSVD_ERR_NOMEM; }
+    memset(&h->stats, 0, sizeof(h->stats));
+    int w = 0;
+    double ms = 0;
+    ghsvd_status s = hz_batch_solve(h->batch, h->device, &h->opts, batch, m, p, n, F, ldf, J, n_plus,
+                                    G, ldg, lambda, V, ldv, sweeps, status, &w, &ms, stream);
+    h->stats.block_width = w;
+    h->stats.ms_total = ms;
+    h->solved = false;          // ghsvd_get_factors refers to single solves
+    cudaSetDevice(prev);
+    return s;
+}

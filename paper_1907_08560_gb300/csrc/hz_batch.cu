@@ -1,0 +1,538 @@
+// hz_batch.cu -- batched solves: many independent pencils of uneven order
+// (k-points of an LAPW computation) advanced together, one outer step of
+// every active pencil per "tick" of the Level-2 block HZ method (Section 6.4).
+//
+// Each pencil keeps its own working buffers, schedule (block partition and
+// round-robin tables, Section 6.3, 6.4.1), transformation counters and state
+// (current outer step, sweep, active flag).  A tick is four launches: the
+// Gram, inner and update kernels over the work items of every pencil (CTAs of
+// inactive pencils return at once), and a control kernel that advances each
+// pencil's step and, at the end of its sweep, applies the stopping rule of
+// Section 6.1.7 to that pencil's own counters.  The ticks are captured in a
+// CUDA graph and replayed until no pencil is active, so the host only reads
+// one counter per replay.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <vector>
+
+#include "../../include/ghsvd.h"
+#include "hz_kernels.cuh"
+#include "hz_launch.h"
+
+namespace hz {
+
+// Per-pencil device descriptor.
+struct BPencil {
+    double2 *W;                 // [ld x n] stacked F', G', Z'
+    long long ld;               // Mt
+    const int8_t *Jrow;         // [m_pad]
+    const int *slot;            // [nsteps][npairs][kk]
+    double2 *partial;           // [npairs][cpp][KKMAX^2]
+    double2 *zhat;              // [npairs][KKMAX^2]
+    int *flag;                  // [npairs]
+    unsigned long long *cnt;    // [2]: all, big of the current sweep
+    int *err;                   // [2]
+    int m_pad, p_pad, n_pad, n;
+    int kk, npairs, nsteps, kc, chunks_h, chunks_s;
+    double tol;
+};
+
+// Per-pencil state, advanced by the control kernel.
+struct BState {
+    int step, sweep, active, status;
+};
+
+// Status codes the control kernel writes (mirror ghsvd_status).
+constexpr int BST_RUNNING = -1;
+
+__global__ void __launch_bounds__(192)
+gram_batched(const BPencil *__restrict__ P, const BState *__restrict__ S, const int4 *__restrict__ work)
+{
+    const int4 w = work[blockIdx.x];
+    if (!S[w.x].active) return;
+    const BPencil &p = P[w.x];
+    const int r = S[w.x].step;
+    const int c = w.z;
+    const bool isH = c < p.chunks_h;
+    const int r0 = isH ? c * p.kc : p.m_pad + (c - p.chunks_h) * p.kc;
+    const int r1 = isH ? min(r0 + p.kc, p.m_pad) : min(r0 + p.kc, p.m_pad + p.p_pad);
+    const int cpp = p.chunks_h + p.chunks_s;
+    gram_body<double>(p.W, p.ld, p.Jrow, p.slot + ((long long)r * p.npairs + w.y) * p.kk, p.kk, r0,
+                      r1, isH, p.partial + ((long long)w.y * cpp + c) * (KKMAX * KKMAX));
+}
+
+__global__ void __launch_bounds__(1024)
+inner_batched(const BPencil *__restrict__ P, const BState *__restrict__ S, const int4 *__restrict__ work,
+              int inner_sweeps, int crit_mode)
+{
+    extern __shared__ unsigned char smraw_inner[];
+    const int4 w = work[blockIdx.x];
+    if (!S[w.x].active) return;
+    const BPencil &p = P[w.x];
+    const int r = S[w.x].step;
+    InnerArgs a;
+    a.npairs = p.npairs;
+    a.kk = p.kk;
+    a.cpp = p.chunks_h + p.chunks_s;
+    a.chunks_h = p.chunks_h;
+    a.inner_sweeps = inner_sweeps;
+    a.crit_mode = crit_mode;
+    a.tol = p.tol;
+    inner_body<double, double>(p.partial + (long long)w.y * a.cpp * (KKMAX * KKMAX),
+                               p.slot + ((long long)r * p.npairs + w.y) * p.kk, a,
+                               p.zhat + (long long)w.y * KKMAX * KKMAX, p.flag + w.y, p.cnt, p.err,
+                               smraw_inner);
+}
+
+__global__ void __launch_bounds__(256)
+update_batched(const BPencil *__restrict__ P, const BState *__restrict__ S, const int4 *__restrict__ work)
+{
+    extern __shared__ unsigned char smraw[];
+    const int4 w = work[blockIdx.x];
+    if (!S[w.x].active) return;
+    const BPencil &p = P[w.x];
+    if (!p.flag[w.y]) return;
+    const int r = S[w.x].step;
+    update_body<double, double>(p.W, p.ld, p.slot + ((long long)r * p.npairs + w.y) * p.kk, p.kk,
+                                (long long)w.z * UPD_R, p.zhat + (long long)w.y * KKMAX * KKMAX, smraw);
+}
+
+// One thread per pencil: advance the step; at the end of a sweep apply the
+// stopping rule (no big transformation, Section 6.1.7) or C_max, record the
+// sweep's counts, reset the counters.  *active_count = pencils still running.
+__global__ void control_batched(const BPencil *__restrict__ P, BState *__restrict__ S, int batch,
+                                int max_sweeps, long long *__restrict__ hist, int hist_len,
+                                int *__restrict__ active_count)
+{
+    __shared__ int count;
+    if (threadIdx.x == 0) count = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < batch; i += blockDim.x) {
+        BState st = S[i];
+        if (st.active) {
+            const BPencil &p = P[i];
+            if (p.err[0] & DEVERR_RANK) { st.active = 0; st.status = GHSVD_ERR_RANK_DEFICIENT; }
+            else if (p.err[0] & DEVERR_NONFINITE) { st.active = 0; st.status = GHSVD_ERR_NONFINITE; }
+            else if (st.step == p.nsteps - 1) {
+                const unsigned long long all = p.cnt[0], big = p.cnt[1];
+                if (st.sweep < hist_len) {
+                    hist[((long long)i * hist_len + st.sweep) * 2] = (long long)all;
+                    hist[((long long)i * hist_len + st.sweep) * 2 + 1] = (long long)big;
+                }
+                st.sweep += 1;
+                p.cnt[0] = 0;
+                p.cnt[1] = 0;
+                st.step = 0;
+                if (big == 0) { st.active = 0; st.status = GHSVD_OK; }
+                else if (st.sweep >= max_sweeps) { st.active = 0; st.status = GHSVD_ERR_NOT_CONVERGED; }
+            } else {
+                st.step += 1;
+            }
+            S[i] = st;
+        }
+        if (st.active) atomicAdd(&count, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *active_count = count;
+}
+
+__global__ void state_init(BState *S, int batch)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < batch) { S[i].step = 0; S[i].sweep = 0; S[i].active = 1; S[i].status = BST_RUNNING; }
+}
+
+}  // namespace hz
+
+using hz::BPencil;
+using hz::BState;
+
+namespace {
+
+long long rup(long long x, long long r) { return (x + r - 1) / r * r; }
+long long a256(long long x) { return rup(x, 256); }
+
+// Host-side plan of one pencil.
+struct PlanP {
+    int m, p, n, m_pad, p_pad, n_pad, nb, wb, kk, npairs, nsteps, kc, chunks_h, chunks_s;
+    long long Mt;
+    long long oW, oPart, oZhat, oFlag, oSlot, oJrow, oCnt, oErr, oLam, oGsc, oVn, oGc, oKap, oRank;
+};
+
+struct Plan {
+    int w;
+    std::vector<PlanP> pp;
+    long long bytes;
+    int gram_work, inner_work, update_work;
+};
+
+int partition(int n, int w, std::vector<int> &off)
+{
+    int nb = (n + w - 1) / w;
+    if (nb & 1) nb += 1;
+    if (nb < 2) nb = 2;
+    if (nb > n) nb = n & ~1;
+    const int wb = (n + nb - 1) / nb;
+    const int wide = n - nb * (wb - 1);
+    off.assign(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) off[b + 1] = off[b] + (b < wide ? wb : wb - 1);
+    return nb;
+}
+
+Plan make_plan(int batch, const int64_t *m, const int64_t *p, const int64_t *n, int w, int sms)
+{
+    Plan pl;
+    pl.w = w;
+    pl.bytes = 0;
+    pl.gram_work = pl.inner_work = pl.update_work = 0;
+    // one Gram row chunk for the whole batch: about 4 Gram CTAs per SM per tick
+    long long pair_rows = 0;
+    for (int i = 0; i < batch; ++i) {
+        std::vector<int> off;
+        const int nbi = partition((int)n[i], std::min<int>(w, (int)n[i]), off);
+        pair_rows += (long long)(nbi / 2) * (rup(m[i], hz::ROWPAD) + rup(p[i], hz::ROWPAD));
+    }
+    const int kc_all = (int)std::min<long long>(4096, std::max<long long>(256, rup(pair_rows / (4LL * sms), 64)));
+    for (int i = 0; i < batch; ++i) {
+        PlanP q{};
+        q.m = (int)m[i]; q.p = (int)p[i]; q.n = (int)n[i];
+        q.m_pad = (int)rup(q.m, hz::ROWPAD); q.p_pad = (int)rup(q.p, hz::ROWPAD);
+        q.n_pad = (int)rup(q.n, hz::ROWPAD);
+        q.Mt = (long long)q.m_pad + q.p_pad + q.n_pad;
+        std::vector<int> off;
+        q.nb = partition(q.n, std::min(w, q.n), off);
+        q.wb = off[1] - off[0];
+        q.kk = 2 * q.wb;
+        q.npairs = q.nb / 2;
+        q.nsteps = q.nb - 1;
+        q.kc = kc_all;
+        q.chunks_h = (q.m_pad + q.kc - 1) / q.kc;
+        q.chunks_s = (q.p_pad + q.kc - 1) / q.kc;
+        const int cpp = q.chunks_h + q.chunks_s;
+        auto carve = [&](long long b) { long long at = pl.bytes; pl.bytes += a256(b); return at; };
+        q.oW = carve(16LL * q.Mt * q.n);
+        q.oPart = carve(16LL * q.npairs * cpp * hz::KKMAX * hz::KKMAX);
+        q.oZhat = carve(16LL * q.npairs * hz::KKMAX * hz::KKMAX);
+        q.oFlag = carve(4LL * q.npairs);
+        q.oSlot = carve(4LL * q.nsteps * q.npairs * q.kk);
+        q.oJrow = carve(q.m_pad);
+        q.oCnt = carve(16);
+        q.oErr = carve(8);
+        q.oLam = carve(8LL * q.n); q.oGsc = carve(8LL * q.n); q.oVn = carve(8LL * q.n);
+        q.oGc = carve(8LL * q.n); q.oKap = carve(8); q.oRank = carve(4LL * q.n);
+        pl.gram_work += q.npairs * cpp;
+        pl.inner_work += q.npairs;
+        pl.update_work += q.npairs * (int)(q.Mt / hz::UPD_R);
+        pl.pp.push_back(q);
+    }
+    return pl;
+}
+
+}  // namespace
+
+// Batched working memory, owned by a handle and reused between calls.
+struct BatchBuffers {
+    unsigned char *arena = nullptr;
+    long long arena_bytes = 0;
+    BPencil *d_pen = nullptr;
+    BState *d_state = nullptr;
+    int4 *d_work = nullptr;
+    long long *d_hist = nullptr;
+    int *d_active = nullptr;
+    int cap_batch = 0;
+    long long cap_work = 0;
+};
+
+static void free_batch(BatchBuffers &b)
+{
+    cudaFree(b.arena); cudaFree(b.d_pen); cudaFree(b.d_state); cudaFree(b.d_work);
+    cudaFree(b.d_hist); cudaFree(b.d_active);
+    b = BatchBuffers();
+}
+
+#define BT_TRY(x)                                               \
+    do {                                                        \
+        cudaError_t e_ = (x);                                   \
+        if (e_ != cudaSuccess) {                                \
+            free_batch(bb);                                     \
+            return e_ == cudaErrorMemoryAllocation ? GHSVD_ERR_NOMEM : GHSVD_ERR_CUDA; \
+        }                                                       \
+    } while (0)
+
+constexpr int kHistLen = 64;
+
+// Set up the working buffers of every pencil for plan pl (copy-in, signs,
+// schedule); returns the device descriptors.
+static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, const void *const *F,
+                                const int64_t *ldf, const int8_t *const *J, const int64_t *n_plus,
+                                const void *const *G, const int64_t *ldg, cudaStream_t st)
+{
+    if (pl.bytes > bb.arena_bytes) {
+        cudaFree(bb.arena);
+        bb.arena = nullptr;
+        bb.arena_bytes = 0;
+        BT_TRY(cudaMalloc((void **)&bb.arena, pl.bytes));
+        bb.arena_bytes = pl.bytes;
+    }
+    if (batch > bb.cap_batch) {
+        cudaFree(bb.d_pen); cudaFree(bb.d_state); cudaFree(bb.d_hist);
+        bb.d_pen = nullptr; bb.d_state = nullptr; bb.d_hist = nullptr;
+        BT_TRY(cudaMalloc((void **)&bb.d_pen, sizeof(BPencil) * batch));
+        BT_TRY(cudaMalloc((void **)&bb.d_state, sizeof(BState) * batch));
+        BT_TRY(cudaMalloc((void **)&bb.d_hist, sizeof(long long) * 2 * kHistLen * batch));
+        bb.cap_batch = batch;
+    }
+    if (!bb.d_active) BT_TRY(cudaMalloc((void **)&bb.d_active, sizeof(int)));
+    const long long nwork = (long long)pl.gram_work + pl.inner_work + pl.update_work;
+    if (nwork > bb.cap_work) {
+        cudaFree(bb.d_work);
+        bb.d_work = nullptr;
+        BT_TRY(cudaMalloc((void **)&bb.d_work, sizeof(int4) * nwork));
+        bb.cap_work = nwork;
+    }
+    std::vector<BPencil> hp(batch);
+    std::vector<int4> work;
+    work.reserve(nwork);
+    for (int i = 0; i < batch; ++i) {
+        const PlanP &q = pl.pp[i];
+        unsigned char *base = bb.arena;
+        BPencil d{};
+        d.W = (double2 *)(base + q.oW);
+        d.ld = q.Mt;
+        d.Jrow = (const int8_t *)(base + q.oJrow);
+        d.slot = (const int *)(base + q.oSlot);
+        d.partial = (double2 *)(base + q.oPart);
+        d.zhat = (double2 *)(base + q.oZhat);
+        d.flag = (int *)(base + q.oFlag);
+        d.cnt = (unsigned long long *)(base + q.oCnt);
+        d.err = (int *)(base + q.oErr);
+        d.m_pad = q.m_pad; d.p_pad = q.p_pad; d.n_pad = q.n_pad; d.n = q.n;
+        d.kk = q.kk; d.npairs = q.npairs; d.nsteps = q.nsteps; d.kc = q.kc;
+        d.chunks_h = q.chunks_h; d.chunks_s = q.chunks_s;
+        d.tol = ldexp(1.0, -53) * sqrt((double)q.n);
+        hp[i] = d;
+        // schedule tables (host-built, as for a single pencil)
+        std::vector<int> off;
+        partition(q.n, std::min(pl.w, q.n), off);
+        std::vector<int> tab((size_t)q.nsteps * q.npairs * q.kk, -1);
+        for (int r = 0; r < q.nsteps; ++r)
+            for (int k = 0; k < q.npairs; ++k) {
+                int P, Q;
+                hz::rr_pair(q.nb, r, k, &P, &Q);
+                int *row = &tab[((size_t)r * q.npairs + k) * q.kk];
+                for (int c = off[P]; c < off[P + 1]; ++c) row[c - off[P]] = c;
+                for (int c = off[Q]; c < off[Q + 1]; ++c) row[q.wb + c - off[Q]] = c;
+            }
+        BT_TRY(cudaMemcpyAsync((void *)d.slot, tab.data(), sizeof(int) * tab.size(),
+                               cudaMemcpyHostToDevice, st));
+        BT_TRY(cudaMemsetAsync(d.cnt, 0, 16, st));
+        BT_TRY(cudaMemsetAsync(d.err, 0, 8, st));
+        BT_TRY(cudaMemsetAsync(d.flag, 0, 4LL * q.npairs, st));
+        BT_TRY(hz::launch_signs((int8_t *)d.Jrow, J ? J[i] : nullptr, q.m, q.m_pad,
+                                n_plus ? n_plus[i] : q.m, d.err + 1, st));
+        BT_TRY(hz::launch_copyin(d.W, false, q.Mt, q.m, q.p, q.n, q.m_pad, q.p_pad, q.n_pad, F[i],
+                                 ldf[i], G[i], ldg[i], nullptr, 0, d.err, st));
+        BT_TRY(hz::launch_gnorm(d.W, q.Mt, q.m_pad, q.p_pad, q.n, (double *)(base + q.oGc), st));
+    }
+    for (int i = 0; i < batch; ++i) {
+        const PlanP &q = pl.pp[i];
+        const int cpp = q.chunks_h + q.chunks_s;
+        for (int k = 0; k < q.npairs; ++k)
+            for (int c = 0; c < cpp; ++c) work.push_back(make_int4(i, k, c, 0));
+    }
+    for (int i = 0; i < batch; ++i)
+        for (int k = 0; k < pl.pp[i].npairs; ++k) work.push_back(make_int4(i, k, 0, 0));
+    for (int i = 0; i < batch; ++i) {
+        const PlanP &q = pl.pp[i];
+        for (int t = 0; t < (int)(q.Mt / hz::UPD_R); ++t)
+            for (int k = 0; k < q.npairs; ++k) work.push_back(make_int4(i, k, t, 0));
+    }
+    BT_TRY(cudaMemcpyAsync(bb.d_pen, hp.data(), sizeof(BPencil) * batch, cudaMemcpyHostToDevice, st));
+    BT_TRY(cudaMemcpyAsync(bb.d_work, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice,
+                           st));
+    BT_TRY(cudaMemsetAsync(bb.d_hist, 0, sizeof(long long) * 2 * kHistLen * batch, st));
+    hz::state_init<<<(batch + 127) / 128, 128, 0, st>>>(bb.d_state, batch);
+    BT_TRY(cudaGetLastError());
+    return GHSVD_OK;
+}
+
+static cudaError_t enqueue_tick(const BatchBuffers &bb, const Plan &pl, int batch, int inner_sweeps,
+                                int crit_mode, int max_sweeps, cudaStream_t st)
+{
+    const int4 *wg = bb.d_work;
+    const int4 *wi = wg + pl.gram_work;
+    const int4 *wu = wi + pl.inner_work;
+    const int gthreads = pl.w * 2 > hz::KKMAX / 2 ? 192 : 64;
+    hz::gram_batched<<<pl.gram_work, gthreads, 0, st>>>(bb.d_pen, bb.d_state, wg);
+    hz::inner_batched<<<pl.inner_work, 1024, 3 * sizeof(double2) * hz::KKMAX * hz::KKMAX, st>>>(
+        bb.d_pen, bb.d_state, wi, inner_sweeps, crit_mode);
+    hz::update_batched<<<pl.update_work, 256, 2 * sizeof(double2) * hz::KKMAX * hz::KKMAX, st>>>(
+        bb.d_pen, bb.d_state, wu);
+    hz::control_batched<<<1, 128, 0, st>>>(bb.d_pen, bb.d_state, batch, max_sweeps, bb.d_hist,
+                                           kHistLen, bb.d_active);
+    return cudaGetLastError();
+}
+
+static cudaError_t batch_attributes()
+{
+    cudaError_t e = cudaFuncSetAttribute(hz::inner_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(3 * sizeof(double2) * hz::KKMAX * hz::KKMAX));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(hz::update_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * sizeof(double2) * hz::KKMAX * hz::KKMAX));
+}
+
+// Run ticks until no pencil is active: a graph of `ticks_per_graph` ticks is
+// captured once and replayed.  Returns the number of ticks launched.
+static ghsvd_status run_ticks(BatchBuffers &bb, const Plan &pl, int batch, const ghsvd_opts &o,
+                              cudaStream_t st, long long max_ticks, long long *ticks_out)
+{
+    const int tpg = 8;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    for (int t = 0; e == cudaSuccess && t < tpg; ++t)
+        e = enqueue_tick(bb, pl, batch, o.inner_sweeps, o.crit_mode, o.max_sweeps, cs);
+    if (e == cudaSuccess) e = cudaStreamEndCapture(cs, &graph);
+    else if (cs) {
+        cudaGraph_t g2 = nullptr;
+        cudaStreamEndCapture(cs, &g2);
+        if (g2) cudaGraphDestroy(g2);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    long long ticks = 0;
+    int active = batch;
+    while (e == cudaSuccess && active > 0 && ticks < max_ticks) {
+        e = cudaGraphLaunch(exec, st);
+        ticks += tpg;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&active, bb.d_active, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+    if (ticks_out) *ticks_out = ticks;
+    if (e != cudaSuccess) return GHSVD_ERR_CUDA;
+    return GHSVD_OK;
+}
+
+void *hz_batch_new() { return new (std::nothrow) BatchBuffers(); }
+
+void hz_batch_free(void *p)
+{
+    if (!p) return;
+    BatchBuffers *b = (BatchBuffers *)p;
+    free_batch(*b);
+    delete b;
+}
+
+ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, int batch,
+                                                 const int64_t *m, const int64_t *p, const int64_t *n,
+                                                 const void *const *F, const int64_t *ldf,
+                                                 const int8_t *const *J, const int64_t *n_plus,
+                                                 const void *const *G, const int64_t *ldg,
+                                                 double *const *lambda, void *const *V,
+                                                 const int64_t *ldv, int *sweeps, int *status,
+                                                 int *w_chosen, double *ms_solve, void *stream)
+{
+    BatchBuffers &bb = *(BatchBuffers *)buffers;
+    const ghsvd_opts &o = *opts;
+    cudaStream_t st = (cudaStream_t)stream;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return GHSVD_ERR_CUDA;
+    if (batch_attributes() != cudaSuccess) return GHSVD_ERR_CUDA;
+
+    // block width: given, or autotuned from a few timed ticks per candidate
+    int w = o.block_width;
+    if (w <= 0) {
+        const int cands[] = {8, 16, 32};
+        double best = 1e300;
+        w = 32;
+        for (int c : cands) {
+            Plan pl = make_plan(batch, m, p, n, c, sms);
+            ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, st);
+            if (s != GHSVD_OK) return s;
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            const int probe = 4;
+            // warm-up tick, then time `probe` ticks
+            enqueue_tick(bb, pl, batch, o.inner_sweeps, o.crit_mode, 1 << 30, st);
+            cudaEventRecord(e0, st);
+            for (int t = 0; t < probe; ++t) enqueue_tick(bb, pl, batch, o.inner_sweeps, o.crit_mode, 1 << 30, st);
+            cudaEventRecord(e1, st);
+            cudaError_t e = cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (e != cudaSuccess) return GHSVD_ERR_CUDA;
+            // time of one sweep of every pencil ~ ticks per sweep x tick time
+            int tps = 0;
+            for (const PlanP &q : pl.pp) tps = std::max(tps, q.nsteps);
+            const double sweep_ms = (double)ms / probe * tps;
+            if (sweep_ms < best) { best = sweep_ms; w = c; }
+        }
+    }
+    if (w_chosen) *w_chosen = w;
+    Plan pl = make_plan(batch, m, p, n, w, sms);
+    auto t0 = std::chrono::steady_clock::now();
+    ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, st);
+    if (s != GHSVD_OK) return s;
+    // bad J entries or non-finite inputs
+    std::vector<int> herr(2 * batch, 0);
+    for (int i = 0; i < batch; ++i)
+        if (cudaMemcpyAsync(&herr[2 * i], bb.arena + pl.pp[i].oErr, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return GHSVD_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GHSVD_ERR_CUDA;
+    for (int i = 0; i < batch; ++i) {
+        if (herr[2 * i + 1]) return GHSVD_ERR_INVALID_ARG;
+        if (herr[2 * i] & hz::DEVERR_NONFINITE) return GHSVD_ERR_NONFINITE;
+    }
+    long long max_ticks = 0;
+    for (const PlanP &q : pl.pp) max_ticks = std::max<long long>(max_ticks, (long long)q.nsteps * o.max_sweeps);
+    long long ticks = 0;
+    s = run_ticks(bb, pl, batch, o, st, max_ticks + 16, &ticks);
+    if (s != GHSVD_OK) return s;
+    std::vector<BState> hs(batch);
+    if (cudaMemcpyAsync(hs.data(), bb.d_state, sizeof(BState) * batch, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return GHSVD_ERR_CUDA;
+    // outputs per pencil (Section 6.1.7)
+    for (int i = 0; i < batch; ++i) {
+        const PlanP &q = pl.pp[i];
+        unsigned char *b = bb.arena;
+        cudaError_t e = hz::launch_finalize(
+            (const double2 *)(b + q.oW), q.Mt, (const int8_t *)(b + q.oJrow), q.m_pad, q.p_pad, q.n,
+            o.sort_ascending, (double *)(b + q.oLam), (double *)(b + q.oGsc), (double *)(b + q.oVn),
+            (const double *)(b + q.oGc), (double *)(b + q.oKap), (int *)(b + q.oRank), lambda[i],
+            V ? (double2 *)V[i] : nullptr, ldv ? ldv[i] : q.n, (int *)(b + q.oErr), st);
+        if (e != cudaSuccess) return GHSVD_ERR_CUDA;
+    }
+    for (int i = 0; i < batch; ++i)
+        if (cudaMemcpyAsync(&herr[2 * i], bb.arena + pl.pp[i].oErr, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return GHSVD_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GHSVD_ERR_CUDA;
+    if (ms_solve)
+        *ms_solve = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    ghsvd_status worst = GHSVD_OK;
+    for (int i = 0; i < batch; ++i) {
+        int stt = hs[i].status;
+        if (stt == hz::BST_RUNNING) stt = GHSVD_ERR_NOT_CONVERGED;
+        if (herr[2 * i] & hz::DEVERR_RANK) stt = GHSVD_ERR_RANK_DEFICIENT;
+        if (herr[2 * i] & hz::DEVERR_NONFINITE) stt = GHSVD_ERR_NONFINITE;
+        if (status) status[i] = stt;
+        if (sweeps) sweeps[i] = hs[i].sweep;
+        if (stt != GHSVD_OK && (worst == GHSVD_OK || worst == GHSVD_ERR_NOT_CONVERGED))
+            worst = (ghsvd_status)stt;
+    }
+    return worst;
+}

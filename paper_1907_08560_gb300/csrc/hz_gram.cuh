@@ -16,28 +16,24 @@ namespace hz {
 // q_r + ty + 8i, columns q_c + tx + 8j).  J enters as a sign flip of the
 // conjugated factor (an integer xor on the sign bits).
 // ---------------------------------------------------------------------------
+// The body, for one (pair, row chunk): rows [r0, r1) of W (ld), the pair's
+// kk slot columns `slot`, J signs applied iff isH; writes the partial to out.
 template <typename T>
-__global__ void __launch_bounds__(192)
-gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict__ Jrow,
-            StepArgs a, typename cplx<T>::t *__restrict__ partial)
+__device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict__ W, long long ld,
+                                          const int8_t *__restrict__ Jrow,
+                                          const int *__restrict__ slot, int kk, int r0, int r1,
+                                          bool isH, typename cplx<T>::t *__restrict__ out)
 {
     using T2 = typename cplx<T>::t;
     using U = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
     __shared__ T2 xs[GRAM_KT][KKMAX];
     __shared__ U sgn[GRAM_KT];
     __shared__ int cols[KKMAX];
-    const int cpp = a.chunks_h + a.chunks_s;
-    const int pair = blockIdx.x / cpp;
-    const int c = blockIdx.x % cpp;
-    const bool isH = c < a.chunks_h;
-    const int r0 = isH ? c * a.kc : a.m_pad + (c - a.chunks_h) * a.kc;
-    const int r1 = isH ? min(r0 + a.kc, a.m_pad) : min(r0 + a.kc, a.m_pad + a.p_pad);
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int quad = tid >> 6, t = tid & 63, tx = t & 7, ty = t >> 3;
     // quadrant 0: (0,0), 1: (0,1), 2: (1,1), in units of 32
     const int qr = quad == 2 ? 32 : 0, qc = quad == 0 ? 0 : 32;
-    const int kk = a.kk;
-    for (int s = tid; s < KKMAX; s += nthr) cols[s] = s < kk ? a.slotcol[pair * kk + s] : -1;
+    for (int s = tid; s < KKMAX; s += nthr) cols[s] = s < kk ? slot[s] : -1;
     const U signbit = (U)1 << (sizeof(T) * 8 - 1);
 
     T accr[4][4], acci[4][4];
@@ -53,7 +49,7 @@ gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict_
             const int r = e % GRAM_KT, s = e / GRAM_KT;
             const int col = cols[s];
             T2 v;
-            if (col >= 0) v = W[(long long)col * a.ld + k0 + r];
+            if (col >= 0) v = W[(long long)col * ld + k0 + r];
             else { v.x = 0; v.y = 0; }
             xs[r][s] = v;
         }
@@ -88,8 +84,7 @@ gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict_
                 }
         }
     }
-    // partial[pair][c][i + KKMAX j] (column-major), computed quadrants only
-    T2 *out = partial + ((long long)pair * cpp + c) * (KKMAX * KKMAX);
+    // out[i + KKMAX j] (column-major), computed quadrants only
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -100,6 +95,22 @@ gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict_
             v.y = acci[i][j];
             out[ii + KKMAX * jj] = v;
         }
+}
+
+// One outer step of one pencil: CTA = (pair, row chunk).
+template <typename T>
+__global__ void __launch_bounds__(192)
+gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict__ Jrow,
+            StepArgs a, typename cplx<T>::t *__restrict__ partial)
+{
+    const int cpp = a.chunks_h + a.chunks_s;
+    const int pair = blockIdx.x / cpp;
+    const int c = blockIdx.x % cpp;
+    const bool isH = c < a.chunks_h;
+    const int r0 = isH ? c * a.kc : a.m_pad + (c - a.chunks_h) * a.kc;
+    const int r1 = isH ? min(r0 + a.kc, a.m_pad) : min(r0 + a.kc, a.m_pad + a.p_pad);
+    gram_body<T>(W, a.ld, Jrow, a.slotcol + pair * a.kk, a.kk, r0, r1, isH,
+                 partial + ((long long)pair * cpp + c) * (KKMAX * KKMAX));
 }
 
 }  // namespace hz

@@ -56,14 +56,16 @@ __device__ __forceinline__ void c_left(T2 &x0, T2 &x1, const T *z)
 // transpose of the upper one (the block pivots are Hermitian).
 // One CTA (1024 threads) per block pivot; H^, S^, Z^ live in shared memory.
 // ---------------------------------------------------------------------------
+// The body, for one block pivot: pp = its cpp Gram partials, slot = its kk
+// slot columns, zo = its Z^ (FP64, ld KKMAX), flag = its "transformed" flag.
 template <typename TP, typename TU>
-__global__ void __launch_bounds__(1024)
-inner_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__restrict__ slotcol,
-             InnerArgs a, double2 *__restrict__ zhat, int *__restrict__ pair_flag,
-             unsigned long long *__restrict__ counters, int *__restrict__ err)
+__device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restrict__ pp,
+                                           const int *__restrict__ slot, InnerArgs a,
+                                           double2 *__restrict__ zo, int *__restrict__ flag,
+                                           unsigned long long *__restrict__ counters,
+                                           int *__restrict__ err, unsigned char *smraw_inner)
 {
     using U2 = typename cplx<TU>::t;
-    extern __shared__ unsigned char smraw_inner[];
     U2 *H = reinterpret_cast<U2 *>(smraw_inner);   // [kk * kk], column-major
     U2 *S = H + KKMAX * KKMAX;
     U2 *Z = S + KKMAX * KKMAX;
@@ -73,15 +75,13 @@ inner_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__rest
     __shared__ int pslot[KKMAX];             // slots of pivot l: 2l, 2l+1
     __shared__ int valid[KKMAX];
     __shared__ int s_all, s_big, s_err, s_sweep;
-    const int pair = blockIdx.x;
     const int tid = threadIdx.x;
     const int kk = a.kk, np = kk / 2;
-    if (tid < KKMAX) valid[tid] = tid < kk ? (slotcol[pair * kk + tid] >= 0) : 0;
+    if (tid < KKMAX) valid[tid] = tid < kk ? (slot[tid] >= 0) : 0;
     if (tid == 0) { s_all = 0; s_big = 0; s_err = 0; }
     __syncthreads();
 
     // sum the partial Grams in chunk order (deterministic, in FP64)
-    const typename cplx<TP>::t *pp = partial + (long long)pair * a.cpp * (KKMAX * KKMAX);
     for (int idx = tid; idx < kk * kk; idx += blockDim.x) {
         const int i = idx % kk, j = idx / kk;
         const bool mirror = i >= KKMAX / 2 && j < KKMAX / 2;   // lower off-diagonal quadrant
@@ -204,19 +204,32 @@ inner_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__rest
     if (my_all) atomicAdd(&s_all, my_all);
     if (my_big) atomicAdd(&s_big, my_big);
     __syncthreads();
-    // Zhat[pair] (kk x kk, column-major, ld KKMAX), FP64
-    double2 *zo = zhat + (long long)pair * KKMAX * KKMAX;
+    // Z^ (kk x kk, column-major, ld KKMAX), FP64
     for (int idx = tid; idx < kk * kk; idx += blockDim.x) {
         const int i = idx % kk, j = idx / kk;
         const U2 v = Z[i + kk * j];
         zo[i + KKMAX * j] = make_double2((double)v.x, (double)v.y);
     }
     if (tid == 0) {
-        pair_flag[pair] = s_all > 0;
+        *flag = s_all > 0;
         if (s_all) atomicAdd(&counters[0], (unsigned long long)s_all);
         if (s_big) atomicAdd(&counters[1], (unsigned long long)s_big);
         if (s_err) atomicOr(err, s_err);
     }
+}
+
+// One outer step of one pencil: CTA = block pivot.
+template <typename TP, typename TU>
+__global__ void __launch_bounds__(1024)
+inner_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__restrict__ slotcol,
+             InnerArgs a, double2 *__restrict__ zhat, int *__restrict__ pair_flag,
+             unsigned long long *__restrict__ counters, int *__restrict__ err)
+{
+    extern __shared__ unsigned char smraw_inner[];
+    const int pair = blockIdx.x;
+    inner_body<TP, TU>(partial + (long long)pair * a.cpp * (KKMAX * KKMAX), slotcol + pair * a.kk, a,
+                       zhat + (long long)pair * KKMAX * KKMAX, pair_flag + pair, counters, err,
+                       smraw_inner);
 }
 
 }  // namespace hz

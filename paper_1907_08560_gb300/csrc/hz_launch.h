@@ -60,3 +60,14 @@ cudaError_t launch_extract(const double2 *W, long long ld, int r0, int rows, int
                            long long ldo, cudaStream_t s);
 
 }  // namespace hz
+
+// Batched solves (hz_batch.cu).
+#include "../../include/ghsvd.h"
+void *hz_batch_new();
+void hz_batch_free(void *buffers);
+ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, int batch,
+                            const int64_t *m, const int64_t *p, const int64_t *n,
+                            const void *const *F, const int64_t *ldf, const int8_t *const *J,
+                            const int64_t *n_plus, const void *const *G, const int64_t *ldg,
+                            double *const *lambda, void *const *V, const int64_t *ldv, int *sweeps,
+                            int *status, int *w_chosen, double *ms_solve, void *stream);

@@ -9,23 +9,20 @@ namespace hz {
 // rows of F, G and Z' (the paper's three ZGEMMs).  One CTA per (64-row tile,
 // pair); pairs whose inner level applied nothing are skipped.
 // ---------------------------------------------------------------------------
+// The body, for one (pair, 64-row tile): rows [row0, row0 + 64) of W (ld)
+// in the pair's kk slot columns `slot`, times its Z^ `zp` (ld KKMAX).
 template <typename T, typename TZ>
-__global__ void __launch_bounds__(256)
-update_kernel(typename cplx<T>::t *__restrict__ W, StepArgs a,
-              const typename cplx<TZ>::t *__restrict__ zhat, const int *__restrict__ pair_flag)
+__device__ __forceinline__ void update_body(typename cplx<T>::t *__restrict__ W, long long ld,
+                                            const int *__restrict__ slot, int kk, long long row0,
+                                            const typename cplx<TZ>::t *__restrict__ zp,
+                                            unsigned char *smraw)
 {
     using T2 = typename cplx<T>::t;
-    extern __shared__ unsigned char smraw[];
     T2 *zs = reinterpret_cast<T2 *>(smraw);          // [KKMAX][KKMAX] row l, col j
     T2 *xs = zs + KKMAX * KKMAX;                      // [UPD_R][KKMAX]
     __shared__ int cols[KKMAX];
-    const int pair = blockIdx.y;
-    if (!pair_flag[pair]) return;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int kk = a.kk;
-    const long long row0 = (long long)blockIdx.x * UPD_R;
-    if (tid < KKMAX) cols[tid] = tid < kk ? a.slotcol[pair * kk + tid] : -1;
-    const typename cplx<TZ>::t *zp = zhat + (long long)pair * KKMAX * KKMAX;
+    if (tid < KKMAX) cols[tid] = tid < kk ? slot[tid] : -1;
     for (int idx = tid; idx < KKMAX * KKMAX; idx += 256) {
         const int l = idx % KKMAX, j = idx / KKMAX;   // zhat column-major
         T2 v;
@@ -38,7 +35,7 @@ update_kernel(typename cplx<T>::t *__restrict__ W, StepArgs a,
         const int r = idx % UPD_R, s = idx / UPD_R;
         const int col = cols[s];
         T2 v;
-        if (col >= 0) v = W[(long long)col * a.ld + row0 + r];
+        if (col >= 0) v = W[(long long)col * ld + row0 + r];
         else { v.x = 0; v.y = 0; }
         xs[r * KKMAX + s] = v;
     }
@@ -78,8 +75,22 @@ update_kernel(typename cplx<T>::t *__restrict__ W, StepArgs a,
     for (int idx = tid; idx < UPD_R * KKMAX; idx += 256) {
         const int r = idx % UPD_R, s = idx / UPD_R;
         const int col = cols[s];
-        if (col >= 0) W[(long long)col * a.ld + row0 + r] = xs[r * KKMAX + s];
+        if (col >= 0) W[(long long)col * ld + row0 + r] = xs[r * KKMAX + s];
     }
+}
+
+// One outer step of one pencil: CTA = (64-row tile, pair); pairs whose inner
+// level applied nothing are skipped.
+template <typename T, typename TZ>
+__global__ void __launch_bounds__(256)
+update_kernel(typename cplx<T>::t *__restrict__ W, StepArgs a,
+              const typename cplx<TZ>::t *__restrict__ zhat, const int *__restrict__ pair_flag)
+{
+    extern __shared__ unsigned char smraw[];
+    const int pair = blockIdx.y;
+    if (!pair_flag[pair]) return;
+    update_body<T, TZ>(W, a.ld, a.slotcol + pair * a.kk, a.kk, (long long)blockIdx.x * UPD_R,
+                       zhat + (long long)pair * KKMAX * KKMAX, smraw);
 }
 
 }  // namespace hz

@@ -91,6 +91,12 @@ def load(path: str | None = None):
     lib.ghsvd_solve_noalloc.restype = c_int
     lib.ghsvd_solve_noalloc.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, i64,
                                         ctypes.POINTER(ghsvd_opts), ctypes.POINTER(c_int), vp]
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    lib.ghsvd_solve_batched.restype = c_int
+    lib.ghsvd_solve_batched.argtypes = [vp, c_int, P64, P64, P64, ctypes.POINTER(vp), P64,
+                                        ctypes.POINTER(vp), P64, ctypes.POINTER(vp), P64,
+                                        ctypes.POINTER(vp), ctypes.POINTER(vp), P64,
+                                        ctypes.POINTER(c_int), ctypes.POINTER(c_int), vp]
     lib.ghsvd_status_string.restype = ctypes.c_char_p
     lib.ghsvd_status_string.argtypes = [c_int]
     if path is None:
@@ -250,6 +256,44 @@ def ghsvd_solve_noalloc(F, J, G, n_plus: int | None = None, opts: ghsvd_opts | N
     return lam, V, sweeps.value, s
 
 
+def ghsvd_solve_batched(h, Fs, Js, Gs, n_plus=None, want_vectors: bool = True, stream=None):
+    """Batched solve of independent pencils (lists of column-major complex128
+    CUDA tensors; Js: list of int8 CUDA tensors or None).  Returns
+    (lambdas, Vs, sweeps, statuses, status)."""
+    import torch
+    b = len(Fs)
+    arr = lambda t, vals: (t * b)(*vals)
+    I64 = ctypes.c_int64
+    m = arr(I64, [F.shape[0] for F in Fs])
+    n = arr(I64, [F.shape[1] for F in Fs])
+    p = arr(I64, [G.shape[0] for G in Gs])
+    ldf = arr(I64, [ld_of(F) for F in Fs])
+    ldg = arr(I64, [ld_of(G) for G in Gs])
+    VP = ctypes.c_void_p
+    Fp = arr(VP, [F.data_ptr() for F in Fs])
+    Gp = arr(VP, [G.data_ptr() for G in Gs])
+    Jkeep = [J.contiguous() if J is not None else None for J in (Js or [None] * b)]
+    Jp = arr(VP, [J.data_ptr() if J is not None else None for J in Jkeep])
+    npl = arr(I64, list(n_plus)) if n_plus is not None else None
+    lams = [torch.empty(F.shape[1], dtype=torch.float64, device=F.device) for F in Fs]
+    lp = arr(VP, [l.data_ptr() for l in lams])
+    Vs, Vp, ldv = None, None, None
+    if want_vectors:
+        Vs = [torch.empty_strided((F.shape[1], F.shape[1]), (1, F.shape[1]), dtype=torch.complex128,
+                                  device=F.device) for F in Fs]
+        Vp = arr(VP, [V.data_ptr() for V in Vs])
+        ldv = arr(I64, [F.shape[1] for F in Fs])
+    sw = (ctypes.c_int * b)()
+    stt = (ctypes.c_int * b)()
+    s = load().ghsvd_solve_batched(h, b, m, p, n, Fp, ldf, Jp if Js is not None else None, npl, Gp,
+                                   ldg, lp, Vp, ldv, sw, stt, _stream_ptr(stream))
+    # per-pencil failures are reported in the statuses; raise only for the
+    # errors that concern the whole call
+    if s in (GHSVD_ERR_INVALID_ARG, GHSVD_ERR_CUDA, GHSVD_ERR_NOMEM):
+        _check(s)
+    return lams, Vs, list(sw), list(stt), s
+
+
 def ghsvd_get_factors(h, m: int, p: int, n: int, device="cuda", stream=None):
     """The transformed F' (m x n), G' (p x n) and Z' (n x n) of the last solve."""
     import torch
@@ -286,6 +330,9 @@ class Solver:
 
     def solve_host(self, F, G, J=None, n_plus: int | None = None, **kw):
         return ghsvd_solve_host(self.h, F, J, G, n_plus=n_plus, **kw)
+
+    def solve_batched(self, Fs, Gs, Js=None, **kw):
+        return ghsvd_solve_batched(self.h, Fs, Js, Gs, **kw)
 
     def factors(self, m, p, n, **kw):
         return ghsvd_get_factors(self.h, m, p, n, **kw)

@@ -1,0 +1,118 @@
+"""Batched solves (ghsvd_solve_batched) against the FP64 oracle, pencil by pencil."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from synth import pencils as P
+from conftest import eig_tol_vec, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gh():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_08560_gb300 import build, ghsvd
+    build.build()
+    return ghsvd
+
+
+def dev(gh, X):
+    return gh.colmajor(torch.from_numpy(np.asarray(X))).cuda()
+
+
+def small_batch():
+    # uneven orders (odd ones bordered), ragged row counts, permuted J, one J = I
+    specs = [(37, 0.3, True), (64, 0.2, False), (90, 0.25, True), (45, 0.0, False),
+             (77, 0.2, True), (128, 0.2, False)]
+    out = []
+    for i, (n, frac, perm) in enumerate(specs):
+        m, p = (3 * n) // 2 + i, 2 * n - i
+        F, J, G = P.svd_pencil(4000 + i, m, p, n, int(round(frac * m)), (1e-2, 1e2), (1e-2, 1e2),
+                               permute_j=perm)
+        out.append((F, J, G))
+    return out
+
+
+@pytest.mark.parametrize("w", [8, 16])
+def test_batched_matches_oracle_per_pencil(gh, w):
+    batch = small_batch()
+    s = gh.Solver(0, block_width=w)
+    lams, Vs, sweeps, statuses, st = s.solve_batched(
+        [dev(gh, F) for F, _, _ in batch], [dev(gh, G) for _, _, G in batch],
+        [torch.from_numpy(J).cuda() for _, J, _ in batch])
+    assert st == gh.GHSVD_OK and all(x == 0 for x in statuses)
+    for (F, J, G), lam, V, sw in zip(batch, lams, Vs, sweeps):
+        ref = oracle.solve(F, G, J, method="blocked", w=w)
+        assert ref["status"] == 0
+        tol = eig_tol_vec(F, G, J, ref["lam"], ref["F"])
+        assert np.all(rel_err(lam.cpu().numpy(), ref["lam"]) < tol)
+        assert abs(sw - ref["sweeps"]) <= 3
+        GV = G @ V.cpu().numpy()
+        assert np.max(np.abs(GV.conj().T @ GV - np.eye(F.shape[1]))) < 1e-8
+
+
+def test_batched_equals_single_pencil_solves(gh):
+    batch = small_batch()[:4]
+    s = gh.Solver(0, block_width=16)
+    lams, _, sweeps, statuses, st = s.solve_batched(
+        [dev(gh, F) for F, _, _ in batch], [dev(gh, G) for _, _, G in batch],
+        [torch.from_numpy(J).cuda() for _, J, _ in batch])
+    for (F, J, G), lam, sw in zip(batch, lams, sweeps):
+        one = gh.Solver(0, block_width=16)
+        l1, _, sw1, st1 = one.solve(dev(gh, F), dev(gh, G), torch.from_numpy(J).cuda())
+        Fp, _, _ = one.factors(F.shape[0], G.shape[0], F.shape[1])
+        tol = eig_tol_vec(F, G, J, l1.cpu().numpy(), Fp.cpu().numpy())
+        assert np.all(rel_err(lam.cpu().numpy(), l1.cpu().numpy()) < tol)
+        assert abs(sw - sw1) <= 2
+
+
+def test_batched_autotuned_block_width(gh):
+    batch = small_batch()
+    s = gh.Solver(0, block_width=0)
+    lams, _, _, statuses, st = s.solve_batched(
+        [dev(gh, F) for F, _, _ in batch], [dev(gh, G) for _, _, G in batch],
+        [torch.from_numpy(J).cuda() for _, J, _ in batch], want_vectors=False)
+    assert st == gh.GHSVD_OK
+    w = s.stats()["block_width"]
+    assert w in (8, 16, 32)
+    for (F, J, G), lam in zip(batch, lams):
+        ref = oracle.solve(F, G, J, method="blocked", w=w)
+        tol = eig_tol_vec(F, G, J, ref["lam"], ref["F"])
+        assert np.all(rel_err(lam.cpu().numpy(), ref["lam"]) < tol)
+
+
+def test_batched_failure_stays_in_its_pencil(gh):
+    batch = small_batch()[:3]
+    F1, J1, G1 = batch[1]
+    G1 = G1.copy()
+    G1[:, 5] = G1[:, 9]                 # rank-deficient G in pencil 1 only
+    batch[1] = (F1, J1, G1)
+    s = gh.Solver(0, block_width=8)
+    lams, _, _, statuses, st = s.solve_batched(
+        [dev(gh, F) for F, _, _ in batch], [dev(gh, G) for _, _, G in batch],
+        [torch.from_numpy(J).cuda() for _, J, _ in batch], want_vectors=False)
+    assert statuses[1] == gh.GHSVD_ERR_RANK_DEFICIENT
+    assert statuses[0] == 0 and statuses[2] == 0
+    assert st == gh.GHSVD_ERR_RANK_DEFICIENT
+    for i in (0, 2):
+        F, J, G = batch[i]
+        ref = oracle.solve(F, G, J, method="blocked", w=8)
+        tol = eig_tol_vec(F, G, J, ref["lam"], ref["F"])
+        assert np.all(rel_err(lams[i].cpu().numpy(), ref["lam"]) < tol)
+
+
+def test_batched_identity_signature_without_J(gh):
+    Fs, Gs, lams_ref = [], [], []
+    for i, n in enumerate((40, 66)):
+        F, J, G, lam = P.known_pencil(300 + i, n + 20, n + 30, n, 0, 0, cond_x=10.0)
+        Fs.append(F); Gs.append(G); lams_ref.append(lam)
+    s = gh.Solver(0, block_width=8)
+    lams, _, _, statuses, st = s.solve_batched([dev(gh, F) for F in Fs], [dev(gh, G) for G in Gs],
+                                               None, want_vectors=False)
+    assert st == gh.GHSVD_OK
+    for lam, ref in zip(lams, lams_ref):
+        assert rel_err(lam.cpu().numpy(), ref).max() < 1e-12
