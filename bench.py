@@ -122,6 +122,96 @@ def make_pencil():
     return pencils.lapw_pencil(N, SEED)
 
 
+def _batch_member(args):
+    n, cond, seed = args
+    from synth import pencils
+    return pencils.batch_pencil(n, cond, seed)
+
+
+def make_batch(count, lo, hi):
+    """The k-point batch: orders uniform in [lo, hi], cond(S) log-uniform in
+    [1e4, 1e10] (synth.pencils.batch_shapes); generated in a spawn pool."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from synth import pencils
+    shapes = pencils.batch_shapes(count, lo=lo, hi=hi)
+    jobs = [(n, c, pencils.SEED_BASE + 4000 + i) for i, (n, c) in enumerate(shapes)]
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    workers = min(len(jobs), os.cpu_count() or 1)
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_batch_member, jobs))
+
+
+def run_batched(args):
+    """Batched k-point solves vs the same pencils solved one by one."""
+    import numpy as np
+    batch = make_batch(args.batch, args.batch_lo, args.batch_hi)   # before any CUDA call
+    import torch
+    from paper_1907_08560_gb300 import build as libbuild
+    from paper_1907_08560_gb300 import ghsvd
+    libbuild.build()
+    torch.cuda.set_device(0)
+    Fs = [ghsvd.colmajor(torch.from_numpy(F)).cuda() for F, _, _ in batch]
+    Gs = [ghsvd.colmajor(torch.from_numpy(G)).cuda() for _, _, G in batch]
+    Js = [torch.from_numpy(J).cuda() for _, J, _ in batch]
+    solver = ghsvd.Solver(0, block_width=0, max_sweeps=args.max_sweeps)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        solver.solve_batched(Fs, Gs, Js, stream=stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        lams, _, sweeps, statuses, st = solver.solve_batched(Fs, Gs, Js, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_batch = e0.elapsed_time(e1) / 1e3 / args.steps
+    w = solver.stats()["block_width"]
+    # the same pencils one by one through ghsvd_solve, same block width
+    one = ghsvd.Solver(0, block_width=w, max_sweeps=args.max_sweeps)
+    one.solve(Fs[0], Gs[0], Js[0], stream=stream)
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    seq = []
+    for F, G, J in zip(Fs, Gs, Js):
+        lam, _, _, _ = one.solve(F, G, J, stream=stream, want_vectors=False)
+        seq.append((lam, one.factors(F.shape[0], G.shape[0], F.shape[1])[0]))
+    s1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = s0.elapsed_time(s1) / 1e3
+    worst = 0.0
+    for (F, J, G), lam, (lam1, Fp) in zip(batch, lams, seq):
+        F1 = Fp.cpu().numpy()
+        amp = (np.einsum("ij,ij->j", F1.conj(), F1).real /
+               np.abs(np.einsum("ij,i,ij->j", F1.conj(), J.astype(np.float64), F1).real))
+        l1 = lam1.cpu().numpy()
+        o = np.argsort(l1)
+        tol = 1e-12 * max(1.0, (1e6 + 1e5) / 1e3) * amp[o]
+        err = np.abs(np.sort(lam.cpu().numpy()) - l1[o]) / np.abs(l1[o])
+        worst = max(worst, float((err / tol).max()))
+    ns = [F.shape[1] for F, _, _ in batch]
+    line = {"metric": f"HZ GHSVD batched solves/s ({len(batch)} k-point pencils, n in "
+                      f"[{args.batch_lo},{args.batch_hi}])",
+            "value": len(batch) / t_batch, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batch of {len(batch)} pencils F 1.5n x n (20% -1 signs), "
+                                   f"G 2n x n, cond(S) log-uniform [1e4,1e10], n uniform "
+                                   f"[{args.batch_lo},{args.batch_hi}] (min {min(ns)}, max {max(ns)})",
+                       "block_width_autotuned": w, "sweeps_min": min(sweeps), "sweeps_max": max(sweeps),
+                       "statuses": sorted(set(statuses))},
+            "sequential": {"value": len(batch) / t_seq, "unit": "solves/s", "seconds": t_seq},
+            "speedup_vs_sequential": t_seq / t_batch,
+            "eig_rel_diff_vs_sequential_over_tol_max": worst, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def traffic_per_launch():
     """DRAM bytes per update launch from the committed ncu capture, or None
     when the kernel source changed since the capture."""
@@ -185,6 +275,109 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_warmstart(args):
+    """Learned warm start on the pencil family (n = 256, F 384 x 256, G 512 x 256,
+    4 relative perturbations of size 0.05): train on the solver's eigenvectors
+    at args.train parameter vectors, then solve args.test held-out pencils
+    from V0 = I, from V(t0) and from the learned V0."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_1907_08560_gb300 import build as libbuild
+    from paper_1907_08560_gb300 import ghsvd
+    from paper_1907_08560_gb300 import warmstart as ws
+    from synth import pencils
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    n = args.family_n
+    if args.family_cond == "lapw":
+        F0, J, G0, Fs, Gs = pencils.pencil_family(n)
+        kappa_sum = 1e6 + 10 ** 5
+    else:
+        F0, J, G0, Fs, Gs = pencils.pencil_family(n, sf=(0.5, 2.0), sg=(0.5, 2.0))
+        kappa_sum = 8.0
+
+    fam = ws.Family(F0, J, G0, Fs, Gs)
+    solver = ghsvd.Solver(0, block_width=32, sort_ascending=1, max_sweeps=args.max_sweeps)
+    _, Vref, _, _ = solver.solve(fam.F0, fam.G0, fam.J)
+    train_t = pencils.family_parameters(args.train, seed=pencils.SEED_BASE + 7)
+    test_t = pencils.family_parameters(args.test, seed=pencils.SEED_BASE + 8)
+    # training data: the solver's own eigenvectors (warm-started from V(t0))
+    t0 = time.perf_counter()
+    _, Vs, sw_train, st_train, _ = ws.solve_many(solver, fam, train_t,
+                                                 V0s=ws.reference_v0(fam, Vref, train_t))
+    T = ws.canonical_targets(Vs, Vref)
+    del Vs
+    t_data = time.perf_counter() - t0
+    scale = float(T.std())
+    net = ghsvd.Mlp(4, 64, T.shape[1], seed=3)
+    X = torch.as_tensor(train_t, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = net.train(X, T / scale, epochs=args.epochs, batch=100, lr=1e-3)
+    t_train = time.perf_counter() - t0
+    del T
+    # held-out solves: warm up once on a small subset, then time each start
+    ws.solve_many(solver, fam, test_t[:8])
+    cold = ws.solve_many(solver, fam, test_t)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    V0r = ws.reference_v0(fam, Vref, test_t)
+    torch.cuda.synchronize()
+    t_ref_prep = time.perf_counter() - t0
+    refr = ws.solve_many(solver, fam, test_t, V0s=V0r)
+    del V0r
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    V0l = ws.predict_v0(net, fam, Vref, test_t, scale)
+    torch.cuda.synchronize()
+    t_pred = time.perf_counter() - t0
+    learned = ws.solve_many(solver, fam, test_t, V0s=V0l)
+    del V0l
+    # equal error: learned vs cold eigenvalues on a sample, per-eigenvalue tolerance
+    one = ghsvd.Solver(0, block_width=32, max_sweeps=args.max_sweeps)
+    worst = 0.0
+    for i in range(0, len(test_t), max(1, len(test_t) // 16)):
+        F, G = fam.at(test_t[i])
+        lam1, _, _, _ = one.solve(F, G, fam.J)
+        Fp, _, _ = one.factors(fam.m, fam.p, fam.n)
+        F1 = Fp.cpu().numpy()
+        amp = (np.einsum("ij,ij->j", F1.conj(), F1).real /
+               np.abs(np.einsum("ij,i,ij->j", F1.conj(), J.astype(np.float64), F1).real))
+        l1 = lam1.cpu().numpy()
+        o = np.argsort(l1)
+        tol = 1e-12 * max(1.0, kappa_sum / 1e3) * amp[o]
+        err = np.abs(np.sort(learned[0][i].cpu().numpy()) - l1[o]) / np.abs(l1[o])
+        worst = max(worst, float((err / tol).max()))
+    n_test = len(test_t)
+    t_cold, t_ref, t_learn = cold[4], refr[4] + t_ref_prep, learned[4] + t_pred
+    line = {"metric": f"HZ GHSVD solves/s with a learned warm start (pencil family n={n}, "
+                      f"{n_test} held-out parameters)",
+            "value": n_test / t_learn, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": t_learn * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (MLP f32)", "data": "synthetic",
+            "config": {"family_singular_values": args.family_cond,
+                       "workload": f"F(t) = F0 + sum t_i F_i, G(t) = G0 + sum t_i G_i, i = 1..4, "
+                                   f"t uniform in [-1,1]^4, F_i = 0.05 F0 E_i, G_i = 0.05 G0 E'_i; "
+                                   f"F {fam.m} x {n}, G {fam.p} x {n}; {len(train_t)} training / "
+                                   f"{n_test} held-out t",
+                       "mlp": "4 -> 64 -> 64 -> 2 n^2, tanh, FP32, Adam",
+                       "epochs": args.epochs, "train_loss": loss, "train_seconds": t_train,
+                       "data_seconds": t_data},
+            "sweeps_mean": {"cold_V0_I": float(np.mean(cold[2])),
+                            "V0_reference_V_t0": float(np.mean(refr[2])),
+                            "V0_learned": float(np.mean(learned[2]))},
+            "solves_per_s": {"cold_V0_I": n_test / t_cold, "V0_reference_V_t0": n_test / t_ref,
+                             "V0_learned": n_test / t_learn},
+            "speedup_vs_cold": t_cold / t_learn, "speedup_vs_reference_start": t_ref / t_learn,
+            "statuses": sorted(set(cold[3] + refr[3] + learned[3])),
+            "eig_rel_diff_vs_cold_over_tol_max": worst}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -196,6 +389,16 @@ def main():
     ap.add_argument("--mixed-steps", type=int, default=1,
                     help="timed solves of the mixed-precision schedule (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["pencil", "batched", "warmstart"], default="pencil")
+    ap.add_argument("--family-n", type=int, default=256)
+    ap.add_argument("--train", type=int, default=1500)
+    ap.add_argument("--test", type=int, default=500)
+    ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--family-cond", choices=["lapw", "mild"], default="lapw",
+                    help="singular values of F0, G0: as the n=2048 pencil, or in [0.5, 2]")
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--batch-lo", type=int, default=256)
+    ap.add_argument("--batch-hi", type=int, default=1536)
     ap.add_argument("--max-sweeps", type=int, default=MAX_SWEEPS,
                     help="C_max; a smaller value truncates the solve (profiling only)")
     args = ap.parse_args()
@@ -206,6 +409,12 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batched":
+        run_batched(args)
+        return
+    if args.workload == "warmstart":
+        run_warmstart(args)
         return
 
     import numpy as np

@@ -183,6 +183,9 @@ void ghsvd_destroy(ghsvd_t h);
  *   J             host array [batch] of device int8 pointers (+-1 each), or
  *                 NULL; a NULL array or entry means positives first with
  *                 n_plus[i] leading +1 signs (n_plus NULL: J = I).
+ *   V0, ldv0      host arrays [batch] of device pointers (complex128 n_i x n_i,
+ *                 nonsingular) and leading dimensions, or NULL V0 / NULL
+ *                 entries: the starting Z' of pencil i (as ghsvd_solve_from).
  *   lambda        host array [batch] of device pointers (n_i doubles each).
  *   V, ldv        host arrays [batch] of device pointers and leading
  *                 dimensions, or NULL V (no eigenvectors).
@@ -197,9 +200,64 @@ void ghsvd_destroy(ghsvd_t h);
 ghsvd_status ghsvd_solve_batched(ghsvd_t h, int batch, const int64_t *m, const int64_t *p,
                                  const int64_t *n, const void *const *F, const int64_t *ldf,
                                  const int8_t *const *J, const int64_t *n_plus,
-                                 const void *const *G, const int64_t *ldg, double *const *lambda,
-                                 void *const *V, const int64_t *ldv, int *sweeps, int *status,
-                                 void *stream);
+                                 const void *const *G, const int64_t *ldg,
+                                 const void *const *V0, const int64_t *ldv0,
+                                 double *const *lambda, void *const *V, const int64_t *ldv,
+                                 int *sweeps, int *status, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start.  The paper has no learned part; Algorithm 1 admits any
+ * starting Z' (the prescaling D in the paper), and ghsvd_solve_from takes
+ * one.  For a family of pencils F(t), G(t) a small MLP trained on the
+ * solver's own eigenvectors predicts V0(t); ghsvd_s_orthonormalize makes it
+ * S-orthonormal; the sweeps then run to the stopping rule of Section 6.1.7.
+ * ------------------------------------------------------------------------ */
+typedef struct ghsvd_mlp *ghsvd_mlp_t;
+
+/* MLP x (n_in) -> tanh(W1 x + b1) (n_hidden) -> tanh(W2 . + b2) (n_hidden)
+ * -> W3 . + b3 (n_out), FP32, parameters initialized from `seed`
+ * (uniform in +-1/sqrt(fan_in), zero biases), on CUDA device `device`. */
+ghsvd_status ghsvd_mlp_create(ghsvd_mlp_t *m, int device, int n_in, int n_hidden, int n_out,
+                              uint64_t seed);
+void ghsvd_mlp_destroy(ghsvd_mlp_t m);
+
+/* The flat FP32 parameter vector [W1 (n_hidden x n_in, row-major), b1, W2,
+ * b2, W3 (n_out x n_hidden), b3]: its length; a copy of the parameters
+ * (what = 0) or of the last gradient (what = 1) into dst (host or device);
+ * replacing the parameters from src (host or device). */
+ghsvd_status ghsvd_mlp_size(ghsvd_mlp_t m, int64_t *count);
+ghsvd_status ghsvd_mlp_get(ghsvd_mlp_t m, int what, float *dst);
+ghsvd_status ghsvd_mlp_set(ghsvd_mlp_t m, const float *src);
+
+/* Y (device, batch x n_out, row-major) = MLP(X) for X (device, batch x n_in). */
+ghsvd_status ghsvd_mlp_forward(ghsvd_mlp_t m, int batch, const float *X, float *Y, void *stream);
+
+/* loss = mean over batch x n_out of (MLP(X) - T)^2 (host out, may be NULL);
+ * its gradient w.r.t. the parameters is left in the gradient vector. */
+ghsvd_status ghsvd_mlp_loss_grad(ghsvd_mlp_t m, int batch, const float *X, const float *T,
+                                 double *loss, void *stream);
+
+/* Adam (beta 0.9, 0.999, eps 1e-8, learning rate lr) over `epochs` passes of
+ * minibatches of `batch` consecutive samples of (X, T) (device, row-major);
+ * *final_loss (may be NULL) = mean loss of the last epoch. */
+ghsvd_status ghsvd_mlp_train(ghsvd_mlp_t m, int n_samples, const float *X, const float *T,
+                             int epochs, int batch, float lr, double *final_loss, void *stream);
+
+/* For each of `count` pairs: V0_i <- V0_i R_i^{-1} with
+ * (G_i V0_i)^* (G_i V0_i) = R_i^* R_i (Cholesky of the n x n Gram of G_i V0_i,
+ * never of S), so that V0_i^* S_i V0_i = I.  G_i is p x n, V0_i n x n,
+ * complex128 column-major device arrays (host arrays of pointers and leading
+ * dimensions), n <= 4096; the factorizations run one CTA per pair.
+ * GHSVD_ERR_RANK_DEFICIENT if some G_i V0_i is numerically rank deficient. */
+ghsvd_status ghsvd_s_orthonormalize(int count, int64_t p, int64_t n, const void *const *G,
+                                    const int64_t *ldg, void *const *V0, const int64_t *ldv0,
+                                    void *stream);
+
+/* V[:, j] *= conj(c_j)/|c_j|, c_j = Vref[:, j]^* V[:, j] (device, complex128,
+ * n x n column-major): aligns the free phase of each eigenvector with a
+ * reference set, so that eigenvectors of nearby pencils can be compared. */
+ghsvd_status ghsvd_align_phases(int64_t n, const void *Vref, int64_t ldr, void *V, int64_t ldv,
+                                void *stream);
 
 /* Size of the device array that ghsvd_solve_noalloc works in (32 MiB). */
 #define GHSVD_NOALLOC_SCRATCH_BYTES (32u << 20)

@@ -648,6 +648,7 @@ extern "C" ghsvd_status ghsvd_solve_batched(ghsvd_t h, int batch, const int64_t 
                                            const int64_t *n, const void *const *F, const int64_t *ldf,
                                            const int8_t *const *J, const int64_t *n_plus,
                                            const void *const *G, const int64_t *ldg,
+                                           const void *const *V0, const int64_t *ldv0,
                                            double *const *lambda, void *const *V, const int64_t *ldv,
                                            int *sweeps, int *status, void *stream)
 {
@@ -664,6 +665,8 @@ extern "C" ghsvd_status ghsvd_solve_batched(ghsvd_t h, int batch, const int64_t 
         if (!is_device_ptr(F[i]) || !is_device_ptr(G[i]) || !is_device_ptr(lambda[i]) ||
             (V && V[i] && !is_device_ptr(V[i])) || (Ji && !is_device_ptr(Ji)))
             return GHSVD_ERR_INVALID_ARG;
+        if (V0 && V0[i] && (!ldv0 || ldv0[i] < n[i] || !is_device_ptr(V0[i])))
+            return GHSVD_ERR_INVALID_ARG;
     }
     int prev = 0;
     cudaGetDevice(&prev);
@@ -674,7 +677,7 @@ extern "C" ghsvd_status ghsvd_solve_batched(ghsvd_t h, int batch, const int64_t 
     int w = 0;
     double ms = 0;
     ghsvd_status s = hz_batch_solve(h->batch, h->device, &h->opts, batch, m, p, n, F, ldf, J, n_plus,
-                                    G, ldg, lambda, V, ldv, sweeps, status, &w, &ms, stream);
+                                    G, ldg, V0, ldv0, lambda, V, ldv, sweeps, status, &w, &ms, stream);
     h->stats.block_width = w;
     h->stats.ms_total = ms;
     h->solved = false;          // ghsvd_get_factors refers to single solves

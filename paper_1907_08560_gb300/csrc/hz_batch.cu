@@ -51,7 +51,7 @@ struct BState {
 // Status codes the control kernel writes (mirror ghsvd_status).
 constexpr int BST_RUNNING = -1;
 
-__global__ void __launch_bounds__(192)
+__global__ void __launch_bounds__(160)
 gram_batched(const BPencil *__restrict__ P, const BState *__restrict__ S, const int4 *__restrict__ work)
 {
     const int4 w = work[blockIdx.x];
@@ -169,6 +169,7 @@ struct Plan {
     int w;
     std::vector<PlanP> pp;
     long long bytes;
+    long long oTmp;             // scratch of the largest W, for W <- W V0
     int gram_work, inner_work, update_work;
 };
 
@@ -231,6 +232,10 @@ Plan make_plan(int batch, const int64_t *m, const int64_t *p, const int64_t *n, 
         pl.update_work += q.npairs * (int)(q.Mt / hz::UPD_R);
         pl.pp.push_back(q);
     }
+    long long tmp = 0;
+    for (const PlanP &q : pl.pp) tmp = std::max(tmp, 16LL * q.Mt * q.n);
+    pl.oTmp = pl.bytes;
+    pl.bytes += a256(tmp);
     return pl;
 }
 
@@ -271,7 +276,8 @@ constexpr int kHistLen = 64;
 // schedule); returns the device descriptors.
 static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, const void *const *F,
                                 const int64_t *ldf, const int8_t *const *J, const int64_t *n_plus,
-                                const void *const *G, const int64_t *ldg, cudaStream_t st)
+                                const void *const *G, const int64_t *ldg, const void *const *V0,
+                                const int64_t *ldv0, cudaStream_t st)
 {
     if (pl.bytes > bb.arena_bytes) {
         cudaFree(bb.arena);
@@ -339,6 +345,11 @@ static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, con
         BT_TRY(hz::launch_copyin(d.W, false, q.Mt, q.m, q.p, q.n, q.m_pad, q.p_pad, q.n_pad, F[i],
                                  ldf[i], G[i], ldg[i], nullptr, 0, d.err, st));
         BT_TRY(hz::launch_gnorm(d.W, q.Mt, q.m_pad, q.p_pad, q.n, (double *)(base + q.oGc), st));
+        if (V0 && V0[i]) {      // warm start: (F V0, G V0) with Z' = V0
+            double2 *tmp = (double2 *)(base + pl.oTmp);
+            BT_TRY(hz::launch_gemm(d.W, q.Mt, (int)q.Mt, V0[i], false, ldv0[i], tmp, q.Mt, q.n, st));
+            BT_TRY(cudaMemcpyAsync(d.W, tmp, 16LL * q.Mt * q.n, cudaMemcpyDeviceToDevice, st));
+        }
     }
     for (int i = 0; i < batch; ++i) {
         const PlanP &q = pl.pp[i];
@@ -368,7 +379,9 @@ static cudaError_t enqueue_tick(const BatchBuffers &bb, const Plan &pl, int batc
     const int4 *wg = bb.d_work;
     const int4 *wi = wg + pl.gram_work;
     const int4 *wu = wi + pl.inner_work;
-    const int gthreads = pl.w * 2 > hz::KKMAX / 2 ? 192 : 64;
+    int kkmax = 2;
+    for (const PlanP &q : pl.pp) kkmax = std::max(kkmax, q.kk);
+    const int gthreads = hz::gram_threads(kkmax);
     hz::gram_batched<<<pl.gram_work, gthreads, 0, st>>>(bb.d_pen, bb.d_state, wg);
     hz::inner_batched<<<pl.inner_work, 1024, 3 * sizeof(double2) * hz::KKMAX * hz::KKMAX, st>>>(
         bb.d_pen, bb.d_state, wi, inner_sweeps, crit_mode);
@@ -439,6 +452,7 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
                                                  const void *const *F, const int64_t *ldf,
                                                  const int8_t *const *J, const int64_t *n_plus,
                                                  const void *const *G, const int64_t *ldg,
+                                                 const void *const *V0, const int64_t *ldv0,
                                                  double *const *lambda, void *const *V,
                                                  const int64_t *ldv, int *sweeps, int *status,
                                                  int *w_chosen, double *ms_solve, void *stream)
@@ -459,7 +473,7 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
         w = 32;
         for (int c : cands) {
             Plan pl = make_plan(batch, m, p, n, c, sms);
-            ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, st);
+            ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, V0, ldv0, st);
             if (s != GHSVD_OK) return s;
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
@@ -486,7 +500,7 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
     if (w_chosen) *w_chosen = w;
     Plan pl = make_plan(batch, m, p, n, w, sms);
     auto t0 = std::chrono::steady_clock::now();
-    ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, st);
+    ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, V0, ldv0, st);
     if (s != GHSVD_OK) return s;
     // bad J entries or non-finite inputs
     std::vector<int> herr(2 * batch, 0);

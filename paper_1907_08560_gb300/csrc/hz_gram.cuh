@@ -10,11 +10,11 @@ namespace hz {
 // One CTA per (pair, row chunk); the CTA writes the partial Gram of its rows;
 // the inner kernel sums the partials in a fixed order.
 //
-// The block pivots are Hermitian, so only the two diagonal 32 x 32 quadrants
-// and the upper off-diagonal one are computed (3 of 4; 1 when kk <= 32).
-// 64 threads per quadrant, each a 4 x 4 tile of complex outputs (rows
-// q_r + ty + 8i, columns q_c + tx + 8j).  J enters as a sign flip of the
-// conjugated factor (an integer xor on the sign bits).
+// The block pivots are Hermitian, so only the 16 x 16 tiles on and above the
+// diagonal are computed (10 of 16 for kk = 64, 3 of 4 for kk = 32): 16 threads
+// per tile, each a 4 x 4 set of complex outputs (rows 16 ti + ly + 4i,
+// columns 16 tj + lx + 4j).  J enters as a sign flip of the conjugated factor
+// (an integer xor on the sign bits).
 // ---------------------------------------------------------------------------
 // The body, for one (pair, row chunk): rows [r0, r1) of W (ld), the pair's
 // kk slot columns `slot`, J signs applied iff isH; writes the partial to out.
@@ -30,9 +30,14 @@ __device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict_
     __shared__ U sgn[GRAM_KT];
     __shared__ int cols[KKMAX];
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int quad = tid >> 6, t = tid & 63, tx = t & 7, ty = t >> 3;
-    // quadrant 0: (0,0), 1: (0,1), 2: (1,1), in units of 32
-    const int qr = quad == 2 ? 32 : 0, qc = quad == 0 ? 0 : 32;
+    // upper-triangular tile (ti, tj) of this thread, row-major order
+    const int nt = (kk + 15) >> 4;
+    const int ntiles = nt * (nt + 1) / 2;
+    const int tile = tid >> 4, lx = tid & 3, ly = (tid >> 2) & 3;
+    const bool active = tile < ntiles;
+    int ti = 0, rem = active ? tile : 0;
+    while (rem >= nt - ti) { rem -= nt - ti; ++ti; }
+    const int qr = 16 * ti, qc = 16 * (ti + rem);
     for (int s = tid; s < KKMAX; s += nthr) cols[s] = s < kk ? slot[s] : -1;
     const U signbit = (U)1 << (sizeof(T) * 8 - 1);
 
@@ -55,13 +60,14 @@ __device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict_
         }
         if (tid < GRAM_KT) sgn[tid] = (isH && Jrow[k0 + tid] < 0) ? signbit : (U)0;
         __syncthreads();
+        if (!active) continue;
 #pragma unroll 4
         for (int k = 0; k < GRAM_KT; ++k) {
             const U sb = sgn[k];
             T2 x[4], y[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                x[i] = xs[k][qr + ty + 8 * i];
+                x[i] = xs[k][qr + ly + 4 * i];
                 if (sizeof(T) == 8) {
                     x[i].x = __longlong_as_double(__double_as_longlong(x[i].x) ^ sb);
                     x[i].y = __longlong_as_double(__double_as_longlong(x[i].y) ^ sb);
@@ -71,7 +77,7 @@ __device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict_
                 }
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) y[j] = xs[k][qc + tx + 8 * j];
+            for (int j = 0; j < 4; ++j) y[j] = xs[k][qc + lx + 4 * j];
             // acc_ij += conj(J x_i) y_j
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -84,12 +90,13 @@ __device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict_
                 }
         }
     }
-    // out[i + KKMAX j] (column-major), computed quadrants only
+    // out[i + KKMAX j] (column-major), computed tiles only
+    if (!active) return;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int ii = qr + ty + 8 * i, jj = qc + tx + 8 * j;
+            const int ii = qr + ly + 4 * i, jj = qc + lx + 4 * j;
             T2 v;
             v.x = accr[i][j];
             v.y = acci[i][j];
@@ -99,7 +106,7 @@ __device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict_
 
 // One outer step of one pencil: CTA = (pair, row chunk).
 template <typename T>
-__global__ void __launch_bounds__(192)
+__global__ void __launch_bounds__(160)
 gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict__ Jrow,
             StepArgs a, typename cplx<T>::t *__restrict__ partial)
 {

@@ -51,9 +51,9 @@ __device__ __forceinline__ void c_left(T2 &x0, T2 &x1, const T *z)
 // complex64 preconditioning sweeps).  The 2x2 parameters (eq. 6.5-6.12) are
 // always computed in FP64 from the pivot entries.
 //
-// The Gram kernel writes the two diagonal 32 x 32 quadrants and the upper
-// off-diagonal one; the lower off-diagonal quadrant is the conjugate
-// transpose of the upper one (the block pivots are Hermitian).
+// The Gram kernel writes the 16 x 16 tiles on and above the diagonal; a tile
+// below the diagonal is the conjugate transpose of its mirror (the block
+// pivots are Hermitian).
 // One CTA (1024 threads) per block pivot; H^, S^, Z^ live in shared memory.
 // ---------------------------------------------------------------------------
 // The body, for one block pivot: pp = its cpp Gram partials, slot = its kk
@@ -84,7 +84,7 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
     // sum the partial Grams in chunk order (deterministic, in FP64)
     for (int idx = tid; idx < kk * kk; idx += blockDim.x) {
         const int i = idx % kk, j = idx / kk;
-        const bool mirror = i >= KKMAX / 2 && j < KKMAX / 2;   // lower off-diagonal quadrant
+        const bool mirror = (i >> 4) > (j >> 4);    // a tile below the diagonal
         const int e = mirror ? j + KKMAX * i : i + KKMAX * j;
         double hr = 0, hi = 0, sr = 0, si = 0;
         for (int c = 0; c < a.chunks_h; ++c) {

@@ -29,6 +29,14 @@ struct InnerArgs {
     double tol;                        // eps * sqrt(n)
 };
 
+// Threads of a Gram CTA: 16 per upper-triangular 16 x 16 tile of the kk x kk pivot.
+inline int gram_threads(int kk)
+{
+    const int nt = (kk + 15) / 16;
+    const int t = 16 * nt * (nt + 1) / 2;
+    return t < 32 ? 32 : t;
+}
+
 // Error flags raised by the device (bitwise or).
 constexpr int DEVERR_RANK = 1;
 constexpr int DEVERR_NONFINITE = 2;
@@ -69,5 +77,5 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
                             const int64_t *m, const int64_t *p, const int64_t *n,
                             const void *const *F, const int64_t *ldf, const int8_t *const *J,
                             const int64_t *n_plus, const void *const *G, const int64_t *ldg,
-                            double *const *lambda, void *const *V, const int64_t *ldv, int *sweeps,
+                            const void *const *V0, const int64_t *ldv0, double *const *lambda, void *const *V, const int64_t *ldv, int *sweeps,
                             int *status, int *w_chosen, double *ms_solve, void *stream);

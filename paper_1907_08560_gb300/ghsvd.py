@@ -95,8 +95,32 @@ def load(path: str | None = None):
     lib.ghsvd_solve_batched.restype = c_int
     lib.ghsvd_solve_batched.argtypes = [vp, c_int, P64, P64, P64, ctypes.POINTER(vp), P64,
                                         ctypes.POINTER(vp), P64, ctypes.POINTER(vp), P64,
+                                        ctypes.POINTER(vp), P64,
                                         ctypes.POINTER(vp), ctypes.POINTER(vp), P64,
                                         ctypes.POINTER(c_int), ctypes.POINTER(c_int), vp]
+    FP = ctypes.POINTER(ctypes.c_float)
+    lib.ghsvd_mlp_create.restype = c_int
+    lib.ghsvd_mlp_create.argtypes = [ctypes.POINTER(vp), c_int, c_int, c_int, c_int, ctypes.c_uint64]
+    lib.ghsvd_mlp_destroy.restype = None
+    lib.ghsvd_mlp_destroy.argtypes = [vp]
+    lib.ghsvd_mlp_size.restype = c_int
+    lib.ghsvd_mlp_size.argtypes = [vp, P64]
+    lib.ghsvd_mlp_get.restype = c_int
+    lib.ghsvd_mlp_get.argtypes = [vp, c_int, vp]
+    lib.ghsvd_mlp_set.restype = c_int
+    lib.ghsvd_mlp_set.argtypes = [vp, vp]
+    lib.ghsvd_mlp_forward.restype = c_int
+    lib.ghsvd_mlp_forward.argtypes = [vp, c_int, vp, vp, vp]
+    lib.ghsvd_mlp_loss_grad.restype = c_int
+    lib.ghsvd_mlp_loss_grad.argtypes = [vp, c_int, vp, vp, ctypes.POINTER(ctypes.c_double), vp]
+    lib.ghsvd_mlp_train.restype = c_int
+    lib.ghsvd_mlp_train.argtypes = [vp, c_int, vp, vp, c_int, c_int, ctypes.c_float,
+                                    ctypes.POINTER(ctypes.c_double), vp]
+    lib.ghsvd_s_orthonormalize.restype = c_int
+    lib.ghsvd_s_orthonormalize.argtypes = [c_int, i64, i64, ctypes.POINTER(vp), P64,
+                                           ctypes.POINTER(vp), P64, vp]
+    lib.ghsvd_align_phases.restype = c_int
+    lib.ghsvd_align_phases.argtypes = [i64, vp, i64, vp, i64, vp]
     lib.ghsvd_status_string.restype = ctypes.c_char_p
     lib.ghsvd_status_string.argtypes = [c_int]
     if path is None:
@@ -256,7 +280,8 @@ def ghsvd_solve_noalloc(F, J, G, n_plus: int | None = None, opts: ghsvd_opts | N
     return lam, V, sweeps.value, s
 
 
-def ghsvd_solve_batched(h, Fs, Js, Gs, n_plus=None, want_vectors: bool = True, stream=None):
+def ghsvd_solve_batched(h, Fs, Js, Gs, n_plus=None, want_vectors: bool = True, stream=None,
+                        V0s=None, sort_outputs=None):
     """Batched solve of independent pencils (lists of column-major complex128
     CUDA tensors; Js: list of int8 CUDA tensors or None).  Returns
     (lambdas, Vs, sweeps, statuses, status)."""
@@ -283,15 +308,157 @@ def ghsvd_solve_batched(h, Fs, Js, Gs, n_plus=None, want_vectors: bool = True, s
                                   device=F.device) for F in Fs]
         Vp = arr(VP, [V.data_ptr() for V in Vs])
         ldv = arr(I64, [F.shape[1] for F in Fs])
+    V0p, ldv0 = None, None
+    if V0s is not None:
+        V0p = arr(VP, [V.data_ptr() if V is not None else None for V in V0s])
+        ldv0 = arr(I64, [ld_of(V) if V is not None else 1 for V in V0s])
     sw = (ctypes.c_int * b)()
     stt = (ctypes.c_int * b)()
     s = load().ghsvd_solve_batched(h, b, m, p, n, Fp, ldf, Jp if Js is not None else None, npl, Gp,
-                                   ldg, lp, Vp, ldv, sw, stt, _stream_ptr(stream))
+                                   ldg, V0p, ldv0, lp, Vp, ldv, sw, stt, _stream_ptr(stream))
     # per-pencil failures are reported in the statuses; raise only for the
     # errors that concern the whole call
     if s in (GHSVD_ERR_INVALID_ARG, GHSVD_ERR_CUDA, GHSVD_ERR_NOMEM):
         _check(s)
     return lams, Vs, list(sw), list(stt), s
+
+
+def ghsvd_mlp_create(n_in, n_hidden, n_out, seed=0, device=0):
+    h = ctypes.c_void_p()
+    _check(load().ghsvd_mlp_create(ctypes.byref(h), device, n_in, n_hidden, n_out, seed))
+    return h
+
+
+def ghsvd_mlp_destroy(h):
+    if h:
+        load().ghsvd_mlp_destroy(h)
+
+
+def ghsvd_mlp_size(h):
+    n = ctypes.c_int64()
+    _check(load().ghsvd_mlp_size(h, ctypes.byref(n)))
+    return n.value
+
+
+def ghsvd_mlp_get(h, what, dst):
+    _check(load().ghsvd_mlp_get(h, what, dst.data_ptr()))
+    return dst
+
+
+def ghsvd_mlp_set(h, src):
+    _check(load().ghsvd_mlp_set(h, src.data_ptr()))
+
+
+def ghsvd_mlp_forward(h, X, Y):
+    _check(load().ghsvd_mlp_forward(h, X.shape[0], X.data_ptr(), Y.data_ptr(), None))
+    return Y
+
+
+def ghsvd_mlp_loss_grad(h, X, T):
+    loss = ctypes.c_double(0.0)
+    _check(load().ghsvd_mlp_loss_grad(h, X.shape[0], X.data_ptr(), T.data_ptr(), ctypes.byref(loss),
+                                      None))
+    return loss.value
+
+
+def ghsvd_mlp_train(h, X, T, epochs, batch, lr):
+    loss = ctypes.c_double(0.0)
+    _check(load().ghsvd_mlp_train(h, X.shape[0], X.data_ptr(), T.data_ptr(), epochs, batch, lr,
+                                  ctypes.byref(loss), None))
+    return loss.value
+
+
+class Mlp:
+    """The warm-start MLP of libghsvd (FP32, tanh, two hidden layers)."""
+
+    def __init__(self, n_in, n_hidden, n_out, seed=0, device=0):
+        self.h = ctypes.c_void_p()
+        _check(load().ghsvd_mlp_create(ctypes.byref(self.h), device, n_in, n_hidden, n_out, seed))
+        self.n_in, self.n_hidden, self.n_out = n_in, n_hidden, n_out
+
+    def size(self):
+        n = ctypes.c_int64()
+        _check(load().ghsvd_mlp_size(self.h, ctypes.byref(n)))
+        return n.value
+
+    def get_params(self):
+        """Copy of the flat parameter vector (torch float32 on the device)."""
+        import torch
+        out = torch.empty(self.size(), dtype=torch.float32, device="cuda")
+        _check(load().ghsvd_mlp_get(self.h, 0, out.data_ptr()))
+        return out
+
+    def set_params(self, vec):
+        import torch
+        vec = vec.to(torch.float32).contiguous().cuda()
+        if vec.numel() != self.size():
+            raise ValueError("parameter vector of the wrong length")
+        _check(load().ghsvd_mlp_set(self.h, vec.data_ptr()))
+
+    def get_grads(self):
+        import torch
+        out = torch.empty(self.size(), dtype=torch.float32, device="cuda")
+        _check(load().ghsvd_mlp_get(self.h, 1, out.data_ptr()))
+        return out
+
+    def forward(self, X):
+        import torch
+        X = X.to(torch.float32).contiguous()
+        Y = torch.empty((X.shape[0], self.n_out), dtype=torch.float32, device=X.device)
+        _check(load().ghsvd_mlp_forward(self.h, X.shape[0], X.data_ptr(), Y.data_ptr(), None))
+        return Y
+
+    def loss_grad(self, X, T):
+        import torch
+        X = X.to(torch.float32).contiguous()
+        T = T.to(torch.float32).contiguous()
+        loss = ctypes.c_double(0.0)
+        _check(load().ghsvd_mlp_loss_grad(self.h, X.shape[0], X.data_ptr(), T.data_ptr(),
+                                          ctypes.byref(loss), None))
+        return loss.value, self.get_grads()
+
+    def train(self, X, T, epochs, batch, lr):
+        import torch
+        X = X.to(torch.float32).contiguous()
+        T = T.to(torch.float32).contiguous()
+        loss = ctypes.c_double(0.0)
+        _check(load().ghsvd_mlp_train(self.h, X.shape[0], X.data_ptr(), T.data_ptr(), epochs,
+                                      batch, lr, ctypes.byref(loss), None))
+        return loss.value
+
+    def close(self):
+        if self.h:
+            load().ghsvd_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ghsvd_s_orthonormalize(Gs, V0s, stream=None):
+    """In place for every pair: V0 <- V0 R^{-1}, (G V0)^* (G V0) = R^* R.
+    Gs, V0s: lists of column-major complex128 CUDA tensors (or single ones)."""
+    if not isinstance(Gs, (list, tuple)):
+        Gs, V0s = [Gs], [V0s]
+    b = len(Gs)
+    VP, I64 = ctypes.c_void_p, ctypes.c_int64
+    gp = (VP * b)(*[G.data_ptr() for G in Gs])
+    vp = (VP * b)(*[V.data_ptr() for V in V0s])
+    lg = (I64 * b)(*[ld_of(G) for G in Gs])
+    lv = (I64 * b)(*[ld_of(V) for V in V0s])
+    _check(load().ghsvd_s_orthonormalize(b, Gs[0].shape[0], Gs[0].shape[1], gp, lg, vp, lv,
+                                         _stream_ptr(stream)))
+    return V0s
+
+
+def ghsvd_align_phases(Vref, V, stream=None):
+    """In place: align the phase of each column of V to the same column of Vref."""
+    _check(load().ghsvd_align_phases(V.shape[1], Vref.data_ptr(), ld_of(Vref), V.data_ptr(),
+                                     ld_of(V), _stream_ptr(stream)))
+    return V
 
 
 def ghsvd_get_factors(h, m: int, p: int, n: int, device="cuda", stream=None):

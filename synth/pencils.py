@@ -145,7 +145,7 @@ def lapw_pencil(n: int = 2048, seed: int = SEED_BASE + 2):
     return svd_pencil(seed, m, p, n, m // 6, (1e-3, 1e3), (10 ** -2.5, 10 ** 2.5))
 
 
-def batch_shapes(count: int = 64, seed: int = SEED_BASE + 4, lo: int = 256, hi: int = 1536):
+def batch_shapes(count: int = 64, lo: int = 256, hi: int = 1536, seed: int = SEED_BASE + 4):
     """Orders n uniform in [lo, hi] and cond(S) log-uniform in [1e4, 1e10]."""
     rng = rng_for(seed)
     ns = rng.integers(lo, hi + 1, size=count)
@@ -159,3 +159,31 @@ def batch_pencil(n: int, cond_s: float, seed: int):
     m, p = (3 * n) // 2, 2 * n
     g = np.sqrt(np.sqrt(cond_s))
     return svd_pencil(seed, m, p, n, int(round(0.2 * m)), (1e-3, 1e3), (1.0 / g, g))
+
+
+def pencil_family(n: int = 256, seed: int = SEED_BASE + 5, eps: float = 0.05, k: int = 4,
+                  sf=(1e-3, 1e3), sg=(10 ** -2.5, 10 ** 2.5)):
+    """An affine family F(t) = F0 + sum_i t_i F_i, G(t) = G0 + sum_i t_i G_i.
+
+    (F0, J, G0) is LAPW-shaped (F 1.5n x n with 1/6 negative signs, G 2n x n)
+    with singular values log-uniform on sf and sg (default: those of the
+    n = 2048 benchmark pencil, cond(S) = 1e10).  The k perturbations are
+    relative, of size eps:
+    F_i = eps F0 E_i and G_i = eps G0 E'_i with E_i, E'_i complex Gaussian
+    n x n matrices scaled by 1/sqrt(2n) (spectral norm about sqrt(2)).
+    Returns (F0, J, G0, [F_i], [G_i])."""
+    m, p = (3 * n) // 2, 2 * n
+    F0, J, G0 = svd_pencil(seed, m, p, n, m // 6, sf, sg)
+    rng = rng_for(seed + 1)
+    Fs, Gs = [], []
+    for _ in range(k):
+        E = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(2.0 * n)
+        Fs.append(np.asfortranarray(eps * (F0 @ E)))
+        E = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(2.0 * n)
+        Gs.append(np.asfortranarray(eps * (G0 @ E)))
+    return F0, J, G0, Fs, Gs
+
+
+def family_parameters(count: int, k: int = 4, seed: int = SEED_BASE + 6) -> np.ndarray:
+    """count parameter vectors t uniform in [-1, 1]^k."""
+    return rng_for(seed).uniform(-1.0, 1.0, size=(count, k))

@@ -1,0 +1,116 @@
+"""The warm-start kernels: MLP forward/backward against the FP64 reference,
+training, S-orthonormalization and phase alignment."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import mlp as ref_mlp
+from synth import pencils as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gh():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_08560_gb300 import build, ghsvd
+    build.build()
+    return ghsvd
+
+
+@pytest.mark.parametrize("nin,nh,nout,B", [(4, 16, 40, 12), (4, 64, 3000, 70), (3, 32, 7, 300)])
+def test_mlp_forward_loss_and_gradient_match_reference(gh, nin, nh, nout, B):
+    net = gh.Mlp(nin, nh, nout, seed=7)
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-1, 1, (B, nin)).astype(np.float32)
+    T = rng.standard_normal((B, nout)).astype(np.float32)
+    theta = net.get_params().cpu().numpy().astype(np.float64)
+    Yg = net.forward(torch.from_numpy(X).cuda()).cpu().numpy()
+    Yr, _ = ref_mlp.forward(theta, X.astype(np.float64), nin, nh, nout)
+    assert np.max(np.abs(Yg - Yr)) < 1e-5 * max(1.0, np.abs(Yr).max())
+    Lg, gg = net.loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
+    Lr, gr = ref_mlp.loss_grad(theta, X.astype(np.float64), T.astype(np.float64), nin, nh, nout)
+    assert abs(Lg - Lr) < 1e-5 * Lr
+    gg = gg.cpu().numpy()
+    assert np.linalg.norm(gg - gr) < 1e-4 * np.linalg.norm(gr)
+
+
+def test_mlp_training_fits_a_smooth_map(gh):
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-1, 1, (512, 4)).astype(np.float32)
+    A = rng.standard_normal((4, 20))
+    T = np.sin(X @ A).astype(np.float32) * 0.5
+    net = gh.Mlp(4, 64, 20, seed=1)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    L0, _ = net.loss_grad(Xd, Td)
+    L1 = net.train(Xd, Td, epochs=300, batch=128, lr=3e-3)
+    assert L1 < 0.02 * L0
+
+
+def test_s_orthonormalize(gh):
+    rng = np.random.default_rng(5)
+    p, n = 90, 37
+    G = rng.standard_normal((p, n)) + 1j * rng.standard_normal((p, n))
+    V0 = np.eye(n) + 0.3 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    Gd = gh.colmajor(torch.from_numpy(G)).cuda()
+    Vd = gh.colmajor(torch.from_numpy(V0)).cuda()
+    gh.ghsvd_s_orthonormalize(Gd, Vd)
+    V = Vd.cpu().numpy()
+    GV = G @ V
+    assert np.max(np.abs(GV.conj().T @ GV - np.eye(n))) < 1e-12
+    # same column spans in order: V0^{-1} V is upper triangular
+    Rinv = np.linalg.solve(V0, V)
+    assert np.max(np.abs(np.tril(Rinv, -1))) < 1e-10 * np.abs(Rinv).max()
+
+
+def test_align_phases(gh):
+    rng = np.random.default_rng(6)
+    n = 50
+    Vref = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    ph = np.exp(1j * rng.uniform(-np.pi, np.pi, n))
+    V = (Vref + 0.01 * rng.standard_normal((n, n))) * ph[None, :]
+    Rd = gh.colmajor(torch.from_numpy(Vref)).cuda()
+    Vd = gh.colmajor(torch.from_numpy(V)).cuda()
+    gh.ghsvd_align_phases(Rd, Vd)
+    Va = Vd.cpu().numpy()
+    c = np.einsum("ij,ij->j", Vref.conj(), Va)
+    assert np.all(np.abs(c.imag) < 1e-12 * np.abs(c)) and np.all(c.real > 0)
+    assert np.allclose(np.abs(Va), np.abs(V))
+
+
+def test_learned_warm_start_end_to_end(gh):
+    # a small well-conditioned family (n = 64, singular values in [0.5, 2]):
+    # train on the solver's own eigenvectors, then the warm-started solves
+    # reach the same eigenvalues in fewer sweeps.  (For the ill-conditioned
+    # benchmark family a start basis must be accurate far beyond what a
+    # regression reaches before it saves sweeps, see the design notes.)
+    from paper_1907_08560_gb300 import warmstart as ws
+    from conftest import eig_tol_vec, rel_err
+    F0, J, G0, Fs, Gs = P.pencil_family(64, seed=P.SEED_BASE + 77, sf=(0.5, 2.0), sg=(0.5, 2.0))
+    fam = ws.Family(F0, J, G0, Fs, Gs)
+    solver = gh.Solver(0, block_width=8, sort_ascending=1, max_sweeps=80)
+    lam0, Vref, _, _ = solver.solve(fam.F0, fam.G0, fam.J)
+    train_t = P.family_parameters(160, seed=11)
+    test_t = P.family_parameters(16, seed=12)
+    _, Vs, _, st, _ = ws.solve_many(solver, fam, train_t, V0s=ws.reference_v0(fam, Vref, train_t))
+    assert all(s == 0 for s in st)
+    T = ws.canonical_targets(Vs, Vref)
+    scale = float(T.std())
+    net = gh.Mlp(4, 64, T.shape[1], seed=3)
+    X = torch.as_tensor(train_t, dtype=torch.float32, device="cuda")
+    loss = net.train(X, T / scale, epochs=400, batch=80, lr=2e-3)
+    assert loss < 0.2
+    cold = ws.solve_many(solver, fam, test_t)
+    learned = ws.solve_many(solver, fam, test_t, V0s=ws.predict_v0(net, fam, Vref, test_t, scale))
+    assert all(s == 0 for s in cold[3]) and all(s == 0 for s in learned[3])
+    assert np.mean(learned[2]) < 0.75 * np.mean(cold[2])
+    one = gh.Solver(0, block_width=8)
+    for t, lam in zip(test_t, learned[0]):
+        F, G = fam.at(t)
+        lr_, _, _, _ = one.solve(F, G, fam.J)
+        Fp, _, _ = one.factors(fam.m, fam.p, fam.n)
+        Fn, Gn = F.cpu().numpy(), G.cpu().numpy()
+        tol = eig_tol_vec(Fn, Gn, J, lr_.cpu().numpy(), Fp.cpu().numpy())
+        assert np.all(rel_err(lam.cpu().numpy(), lr_.cpu().numpy()) < tol)
