@@ -76,6 +76,7 @@ struct ghsvd_ctx {
     ghsvd_stats stats{};
     KTimer timer;
     void *batch = nullptr;              // working memory of ghsvd_solve_batched
+    hz::GemmItem *d_item = nullptr;     // one item of the compensated warm-start product
 };
 
 // ---------------------------------------------------------------------------
@@ -113,6 +114,8 @@ static void free_all(ghsvd_ctx *h)
     h->timer.release();
     hz_batch_free(h->batch);
     h->batch = nullptr;
+    cudaFree(h->d_item);
+    h->d_item = nullptr;
     cudaFree(h->W); cudaFree(h->W32); cudaFree(h->Wtmp); cudaFree(h->partial); cudaFree(h->zhat);
     cudaFree(h->pair_flag); cudaFree(h->slotcol); cudaFree(h->Jrow); cudaFree(h->Jdev);
     cudaFree(h->counters); cudaFree(h->err); cudaFree(h->lam_tmp); cudaFree(h->gscale);
@@ -383,8 +386,21 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
     if (V0) {
         // warm start: the sweeps run on (F V0, G V0) and start from Z' = V0
         // (Algorithm 1 admits any nonsingular starting Z')
+        // (compensated sums: the basis may be ill-conditioned)
         CUDA_TRY(grow(&h->Wtmp, Mt * n, &h->cap_wtmp));
-        CUDA_TRY(hz::launch_gemm(h->W, Mt, (int)Mt, V0, false, ldv0, h->Wtmp, Mt, n, st));
+        if (!h->d_item) CUDA_TRY(cudaMalloc((void **)&h->d_item, sizeof(hz::GemmItem) + 8));
+        double *d_kap = (double *)(h->d_item + 1);
+        const hz::GemmItem probe{(const double2 *)V0, ldv0, n, (const double2 *)h->gcol2, 0, nullptr, 0,
+                                 n, 0};
+        double kap = 0.0;
+        CUDA_TRY(cudaMemcpyAsync(h->d_item, &probe, sizeof(probe), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(hz::launch_v0_kappa(h->d_item, 1, d_kap, st));
+        CUDA_TRY(cudaMemcpyAsync(&kap, d_kap, 8, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        const hz::GemmItem item{h->W, Mt, Mt, (const double2 *)V0, ldv0, h->Wtmp, Mt, n,
+                                !(kap <= hz::WARM_ACCURATE_KAPPA)};
+        CUDA_TRY(cudaMemcpyAsync(h->d_item, &item, sizeof(item), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(hz::launch_gemm_batched(h->d_item, 1, Mt, n, st));
         h->stats.kernel_launches += 1;
         CUDA_TRY(cudaMemcpyAsync(h->W, h->Wtmp, sizeof(double2) * Mt * n, cudaMemcpyDeviceToDevice, st));
     }

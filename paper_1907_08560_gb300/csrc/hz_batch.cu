@@ -163,13 +163,15 @@ struct PlanP {
     int m, p, n, m_pad, p_pad, n_pad, nb, wb, kk, npairs, nsteps, kc, chunks_h, chunks_s;
     long long Mt;
     long long oW, oPart, oZhat, oFlag, oSlot, oJrow, oCnt, oErr, oLam, oGsc, oVn, oGc, oKap, oRank;
+    long long oTmp;             // W V0 of this pencil (warm starts only), or -1
 };
 
 struct Plan {
     int w;
     std::vector<PlanP> pp;
     long long bytes;
-    long long oTmp;             // scratch of the largest W, for W <- W V0
+    long long oItems;           // GemmItem[batch] for the warm-start products
+    long long oKap0;            // double[batch]: condition estimates of the V0
     int gram_work, inner_work, update_work;
 };
 
@@ -186,7 +188,8 @@ int partition(int n, int w, std::vector<int> &off)
     return nb;
 }
 
-Plan make_plan(int batch, const int64_t *m, const int64_t *p, const int64_t *n, int w, int sms)
+Plan make_plan(int batch, const int64_t *m, const int64_t *p, const int64_t *n, int w, int sms,
+               bool with_v0)
 {
     Plan pl;
     pl.w = w;
@@ -227,15 +230,16 @@ Plan make_plan(int batch, const int64_t *m, const int64_t *p, const int64_t *n, 
         q.oErr = carve(8);
         q.oLam = carve(8LL * q.n); q.oGsc = carve(8LL * q.n); q.oVn = carve(8LL * q.n);
         q.oGc = carve(8LL * q.n); q.oKap = carve(8); q.oRank = carve(4LL * q.n);
+        q.oTmp = with_v0 ? carve(16LL * q.Mt * q.n) : -1;
         pl.gram_work += q.npairs * cpp;
         pl.inner_work += q.npairs;
         pl.update_work += q.npairs * (int)(q.Mt / hz::UPD_R);
         pl.pp.push_back(q);
     }
-    long long tmp = 0;
-    for (const PlanP &q : pl.pp) tmp = std::max(tmp, 16LL * q.Mt * q.n);
-    pl.oTmp = pl.bytes;
-    pl.bytes += a256(tmp);
+    pl.oItems = pl.bytes;
+    pl.bytes += a256((long long)sizeof(hz::GemmItem) * batch);
+    pl.oKap0 = pl.bytes;
+    pl.bytes += a256(8LL * batch);
     return pl;
 }
 
@@ -345,10 +349,48 @@ static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, con
         BT_TRY(hz::launch_copyin(d.W, false, q.Mt, q.m, q.p, q.n, q.m_pad, q.p_pad, q.n_pad, F[i],
                                  ldf[i], G[i], ldg[i], nullptr, 0, d.err, st));
         BT_TRY(hz::launch_gnorm(d.W, q.Mt, q.m_pad, q.p_pad, q.n, (double *)(base + q.oGc), st));
-        if (V0 && V0[i]) {      // warm start: (F V0, G V0) with Z' = V0
-            double2 *tmp = (double2 *)(base + pl.oTmp);
-            BT_TRY(hz::launch_gemm(d.W, q.Mt, (int)q.Mt, V0[i], false, ldv0[i], tmp, q.Mt, q.n, st));
-            BT_TRY(cudaMemcpyAsync(d.W, tmp, 16LL * q.Mt * q.n, cudaMemcpyDeviceToDevice, st));
+    }
+    // warm starts: (F V0, G V0) with Z' = V0 for every pencil that has a V0,
+    // as one batched FP64 product and one batched copy
+    if (V0) {
+        std::vector<hz::GemmItem> items, back, probe;
+        long long max_rows = 0;
+        int max_n = 0;
+        hz::GemmItem *d_items = (hz::GemmItem *)(bb.arena + pl.oItems);
+        double *d_kap = (double *)(bb.arena + pl.oKap0);
+        // condition estimate of every basis: compensated products only where needed
+        for (int i = 0; i < batch; ++i)
+            if (V0[i])
+                probe.push_back({(const double2 *)V0[i], ldv0[i], pl.pp[i].n,
+                                 (const double2 *)(bb.arena + pl.pp[i].oGc), 0, nullptr, 0,
+                                 pl.pp[i].n, 0});
+        std::vector<double> kap(probe.size(), 0.0);
+        if (!probe.empty()) {
+            BT_TRY(cudaMemcpyAsync(d_items, probe.data(), sizeof(hz::GemmItem) * probe.size(),
+                                   cudaMemcpyHostToDevice, st));
+            BT_TRY(hz::launch_v0_kappa(d_items, (int)probe.size(), d_kap, st));
+            BT_TRY(cudaMemcpyAsync(kap.data(), d_kap, 8 * kap.size(), cudaMemcpyDeviceToHost, st));
+            BT_TRY(cudaStreamSynchronize(st));
+        }
+        size_t kidx = 0;
+        for (int i = 0; i < batch; ++i) {
+            if (!V0[i]) continue;
+            const PlanP &q = pl.pp[i];
+            double2 *Wi = (double2 *)(bb.arena + q.oW);
+            double2 *Ti = (double2 *)(bb.arena + q.oTmp);
+            const int acc = !(kap[kidx++] <= hz::WARM_ACCURATE_KAPPA);
+            items.push_back({Wi, q.Mt, q.Mt, (const double2 *)V0[i], ldv0[i], Ti, q.Mt, q.n, acc});
+            back.push_back({Ti, q.Mt, q.Mt, nullptr, 0, Wi, q.Mt, q.n, 0});
+            max_rows = std::max(max_rows, q.Mt);
+            max_n = std::max(max_n, q.n);
+        }
+        if (!items.empty()) {
+            BT_TRY(cudaMemcpyAsync(d_items, items.data(), sizeof(hz::GemmItem) * items.size(),
+                                   cudaMemcpyHostToDevice, st));
+            BT_TRY(hz::launch_gemm_batched(d_items, (int)items.size(), max_rows, max_n, st));
+            BT_TRY(cudaMemcpyAsync(d_items, back.data(), sizeof(hz::GemmItem) * back.size(),
+                                   cudaMemcpyHostToDevice, st));
+            BT_TRY(hz::launch_copy_batched(d_items, (int)back.size(), st));
         }
     }
     for (int i = 0; i < batch; ++i) {
@@ -472,7 +514,7 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
         double best = 1e300;
         w = 32;
         for (int c : cands) {
-            Plan pl = make_plan(batch, m, p, n, c, sms);
+            Plan pl = make_plan(batch, m, p, n, c, sms, V0 != nullptr);
             ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, V0, ldv0, st);
             if (s != GHSVD_OK) return s;
             cudaEvent_t e0, e1;
@@ -498,7 +540,7 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
         }
     }
     if (w_chosen) *w_chosen = w;
-    Plan pl = make_plan(batch, m, p, n, w, sms);
+    Plan pl = make_plan(batch, m, p, n, w, sms, V0 != nullptr);
     auto t0 = std::chrono::steady_clock::now();
     ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, V0, ldv0, st);
     if (s != GHSVD_OK) return s;

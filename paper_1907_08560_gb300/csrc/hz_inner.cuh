@@ -1,8 +1,35 @@
 // hz_inner.cuh -- the inner level on the block pivots of one outer step (Section 6.4.2).
 #pragma once
+#include <cooperative_groups.h>
+
 #include "hz_common.cuh"
 
 namespace hz {
+
+// Synchronization and replicated stores of the inner level.  With CL = 1 the
+// block pivot lives in one CTA; with CL > 1 a thread-block cluster of CL CTAs
+// (on CL SMs) keeps one copy of (H^, S^, Z^) in each CTA's shared memory, every
+// CTA transforms 1/CL of the entries and stores each result into all CL copies
+// through distributed shared memory.
+template <int CL>
+struct InnerSync {
+    __device__ __forceinline__ static int rank()
+    {
+        if constexpr (CL == 1) return 0;
+        else return (int)cooperative_groups::this_cluster().block_rank();
+    }
+    __device__ __forceinline__ static void sync()
+    {
+        if constexpr (CL == 1) __syncthreads();
+        else cooperative_groups::this_cluster().sync();
+    }
+    template <typename T>
+    __device__ __forceinline__ static T *remote(T *local, int r)
+    {
+        if constexpr (CL == 1) return local;
+        else return cooperative_groups::this_cluster().map_shared_rank(local, (unsigned)r);
+    }
+};
 
 // Complex helpers for the shared-memory block pivots (T = double or float).
 template <typename T2, typename T>
@@ -58,7 +85,7 @@ __device__ __forceinline__ void c_left(T2 &x0, T2 &x1, const T *z)
 // ---------------------------------------------------------------------------
 // The body, for one block pivot: pp = its cpp Gram partials, slot = its kk
 // slot columns, zo = its Z^ (FP64, ld KKMAX), flag = its "transformed" flag.
-template <typename TP, typename TU>
+template <typename TP, typename TU, int CL = 1>
 __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restrict__ pp,
                                            const int *__restrict__ slot, InnerArgs a,
                                            double2 *__restrict__ zo, int *__restrict__ flag,
@@ -66,9 +93,21 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                                            int *__restrict__ err, unsigned char *smraw_inner)
 {
     using U2 = typename cplx<TU>::t;
+    using X = InnerSync<CL>;
     U2 *H = reinterpret_cast<U2 *>(smraw_inner);   // [kk * kk], column-major
     U2 *S = H + KKMAX * KKMAX;
     U2 *Z = S + KKMAX * KKMAX;
+    const int crank = X::rank();
+    // the CL copies of the block pivot (H^, S^, Z^ are consecutive)
+    U2 *copies[CL];
+#pragma unroll
+    for (int r = 0; r < CL; ++r) copies[r] = X::remote(H, r);
+    // A[off] = v in every copy; off is an offset from H
+    auto put = [&](int off, U2 v) {
+#pragma unroll
+        for (int r = 0; r < CL; ++r) copies[r][off] = v;
+    };
+    const int HS = KKMAX * KKMAX;               // offset of S from H (Z: 2 HS)
     __shared__ double zp[KKMAX / 2][8];      // the step's 2x2 transformations (FP64)
     __shared__ TU zu[KKMAX / 2][8];          // the same in the update type
     __shared__ int tr[KKMAX / 2];            // pivot transformed?
@@ -79,10 +118,13 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
     const int kk = a.kk, np = kk / 2;
     if (tid < KKMAX) valid[tid] = tid < kk ? (slot[tid] >= 0) : 0;
     if (tid == 0) { s_all = 0; s_big = 0; s_err = 0; }
-    __syncthreads();
+    // every CTA of the cluster has started before any shared-memory copy is
+    // written from another CTA
+    X::sync();
 
-    // sum the partial Grams in chunk order (deterministic, in FP64)
-    for (int idx = tid; idx < kk * kk; idx += blockDim.x) {
+    // sum the partial Grams in chunk order (deterministic, in FP64); each
+    // CTA of a cluster sums 1/CL of the entries and stores them in all copies
+    for (int idx = tid * CL + crank; idx < kk * kk; idx += CL * blockDim.x) {
         const int i = idx % kk, j = idx / kk;
         const bool mirror = (i >> 4) > (j >> 4);    // a tile below the diagonal
         const int e = mirror ? j + KKMAX * i : i + KKMAX * j;
@@ -100,11 +142,11 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
             hi = 0; si = 0;
             if (!valid[i]) { sr = 1.0; hr = 0.0; }
         }
-        H[i + kk * j] = c_make<U2, TU>((TU)hr, (TU)hi);
-        S[i + kk * j] = c_make<U2, TU>((TU)sr, (TU)si);
-        Z[i + kk * j] = c_make<U2, TU>((TU)(i == j ? 1 : 0), (TU)0);
+        put(i + kk * j, c_make<U2, TU>((TU)hr, (TU)hi));
+        put(HS + i + kk * j, c_make<U2, TU>((TU)sr, (TU)si));
+        put(2 * HS + i + kk * j, c_make<U2, TU>((TU)(i == j ? 1 : 0), (TU)0));
     }
-    __syncthreads();
+    X::sync();
 
     int my_all = 0, my_big = 0;
     for (int isw = 0; isw < a.inner_sweeps; ++isw) {
@@ -143,11 +185,15 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                 }
                 if (step_all) atomicAdd(&s_sweep, step_all);
             }
-            __syncthreads();
-            // two-sided update of H^ and S^ by 2x2 blocks (I <= J), and Z^ <- Z^ Z'
+            // every copy must be read by phase A before any CTA overwrites it
+            X::sync();
+            // two-sided update of H^ and S^ by 2x2 blocks (I <= J), and Z^ <- Z^ Z';
+            // each item owns the entries it writes, so items of different CTAs
+            // never touch the same entry; items are dealt round-robin to the
+            // CTAs of a cluster
             const int nblk = np * (np + 1) / 2;
             const int nitems = 2 * nblk + kk * np;
-            for (int it = tid; it < nitems; it += blockDim.x) {
+            for (int it = tid * CL + crank; it < nitems; it += CL * blockDim.x) {
                 if (it < 2 * nblk) {
                     const int mat = it >= nblk;
                     int b = it - mat * nblk;
@@ -157,6 +203,7 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                     const int Jb = I + b;
                     if (!tr[I] && !tr[Jb]) continue;
                     U2 *A = mat ? S : H;
+                    const int ab = mat ? HS : 0;
                     const int aI = pslot[2 * I], bI = pslot[2 * I + 1];
                     const int aJ = pslot[2 * Jb], bJ = pslot[2 * Jb + 1];
                     U2 x00 = A[aI + kk * aJ], x01 = A[aI + kk * bJ];
@@ -174,13 +221,13 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                         x11.y = 0;
                         x10 = c_make<U2, TU>(x01.x, -x01.y);
                     }
-                    A[aI + kk * aJ] = x00; A[aI + kk * bJ] = x01;
-                    A[bI + kk * aJ] = x10; A[bI + kk * bJ] = x11;
+                    put(ab + aI + kk * aJ, x00); put(ab + aI + kk * bJ, x01);
+                    put(ab + bI + kk * aJ, x10); put(ab + bI + kk * bJ, x11);
                     if (I != Jb) {
-                        A[aJ + kk * aI] = c_make<U2, TU>(x00.x, -x00.y);
-                        A[bJ + kk * aI] = c_make<U2, TU>(x01.x, -x01.y);
-                        A[aJ + kk * bI] = c_make<U2, TU>(x10.x, -x10.y);
-                        A[bJ + kk * bI] = c_make<U2, TU>(x11.x, -x11.y);
+                        put(ab + aJ + kk * aI, c_make<U2, TU>(x00.x, -x00.y));
+                        put(ab + bJ + kk * aI, c_make<U2, TU>(x01.x, -x01.y));
+                        put(ab + aJ + kk * bI, c_make<U2, TU>(x10.x, -x10.y));
+                        put(ab + bJ + kk * bI, c_make<U2, TU>(x11.x, -x11.y));
                     }
                 } else {
                     const int q = it - 2 * nblk;
@@ -189,11 +236,11 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                     const int pa = pslot[2 * l], pb = pslot[2 * l + 1];
                     U2 u = Z[row + kk * pa], w = Z[row + kk * pb];
                     c_right<U2, TU>(u, w, zu[l]);
-                    Z[row + kk * pa] = u;
-                    Z[row + kk * pb] = w;
+                    put(2 * HS + row + kk * pa, u);
+                    put(2 * HS + row + kk * pb, w);
                 }
             }
-            __syncthreads();
+            X::sync();
         }
         // FB: stop after an inner sweep without any transformation
         // (Section 6.1.7, the inner levels count all transformations)
@@ -204,13 +251,14 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
     if (my_all) atomicAdd(&s_all, my_all);
     if (my_big) atomicAdd(&s_big, my_big);
     __syncthreads();
-    // Z^ (kk x kk, column-major, ld KKMAX), FP64
-    for (int idx = tid; idx < kk * kk; idx += blockDim.x) {
+    // Z^ (kk x kk, column-major, ld KKMAX), FP64; the copies are identical,
+    // each CTA of a cluster writes 1/CL of the entries
+    for (int idx = tid * CL + crank; idx < kk * kk; idx += CL * blockDim.x) {
         const int i = idx % kk, j = idx / kk;
         const U2 v = Z[i + kk * j];
         zo[i + KKMAX * j] = make_double2((double)v.x, (double)v.y);
     }
-    if (tid == 0) {
+    if (tid == 0 && crank == 0) {
         *flag = s_all > 0;
         if (s_all) atomicAdd(&counters[0], (unsigned long long)s_all);
         if (s_big) atomicAdd(&counters[1], (unsigned long long)s_big);
@@ -230,6 +278,20 @@ inner_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__rest
     inner_body<TP, TU>(partial + (long long)pair * a.cpp * (KKMAX * KKMAX), slotcol + pair * a.kk, a,
                        zhat + (long long)pair * KKMAX * KKMAX, pair_flag + pair, counters, err,
                        smraw_inner);
+}
+
+// The same with a cluster of CL CTAs per block pivot (grid = npairs * CL).
+template <typename TP, typename TU, int CL>
+__global__ void __launch_bounds__(1024)
+inner_cluster_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__restrict__ slotcol,
+                     InnerArgs a, double2 *__restrict__ zhat, int *__restrict__ pair_flag,
+                     unsigned long long *__restrict__ counters, int *__restrict__ err)
+{
+    extern __shared__ unsigned char smraw_inner[];
+    const int pair = blockIdx.x / CL;
+    inner_body<TP, TU, CL>(partial + (long long)pair * a.cpp * (KKMAX * KKMAX), slotcol + pair * a.kk,
+                           a, zhat + (long long)pair * KKMAX * KKMAX, pair_flag + pair, counters, err,
+                           smraw_inner);
 }
 
 }  // namespace hz

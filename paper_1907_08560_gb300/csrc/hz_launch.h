@@ -41,7 +41,29 @@ inline int gram_threads(int kk)
 constexpr int DEVERR_RANK = 1;
 constexpr int DEVERR_NONFINITE = 2;
 
+// One item of a batched FP64 product C = A B (A rows x n, B n x n, C rows x n,
+// column-major); the batched copy uses A as source and C as destination.
+struct GemmItem {
+    const double2 *A;
+    long long lda;
+    long long rows;
+    const double2 *B;
+    long long ldb;
+    double2 *C;
+    long long ldc;
+    int n;
+    int accurate;       // 1: compensated sums (error-free products and sums), 0: plain FP64
+};
+
 cudaError_t setup_kernels();
+cudaError_t launch_gemm_batched(const GemmItem *items, int count, long long max_rows, int max_n,
+                                cudaStream_t s);
+cudaError_t launch_copy_batched(const GemmItem *items, int count, cudaStream_t s);
+cudaError_t launch_v0_kappa(const GemmItem *items, int count, double *kappa, cudaStream_t s);
+
+// A warm-start basis whose estimated condition relative to G exceeds this is
+// applied with compensated sums (see gemm_batched_kernel).
+constexpr double WARM_ACCURATE_KAPPA = 100.0;
 cudaError_t launch_copyin(void *W, bool single, long long ld, int m, int p, int n, int m_pad,
                           int p_pad, int n_pad, const void *F, long long ldf, const void *G,
                           long long ldg, const void *V0, long long ldv0, int *err, cudaStream_t s);

@@ -3,6 +3,7 @@
 // kernels.  Host code calls only the launch_* functions of hz_launch.h.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "hz_kernels.cuh"
 #include "hz_launch.h"
@@ -281,6 +282,145 @@ gemm_kernel(const double2 *__restrict__ A, long long lda, const TB *__restrict__
         }
 }
 
+// s + c += x * y without losing the rounding errors of the product and of
+// the sum: the product by fma (TwoProduct) and the sum by Knuth's TwoSum, the
+// errors accumulated in c (the compensated dot product of Ogita, Rump and
+// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005).
+__device__ __forceinline__ void acc2(double &s, double &c, double x, double y)
+{
+    const double h = x * y;
+    const double l = fma(x, y, -h);
+    const double t = s + h;
+    const double z = t - s;
+    const double e = (s - (t - z)) + (h - z);
+    s = t;
+    c += e + l;
+}
+
+// Batched form of the same product over independent items (one per pencil),
+// with row and column bounds (any row count): C_i = A_i B_i.  Items marked
+// accurate accumulate with compensated sums, so that the computed product is
+// close to the correctly rounded one even when B_i is ill-conditioned (used
+// to apply a warm-start basis: a plain product would put a backward error of
+// the order of cond(B_i) eps into the factors).
+__global__ void __launch_bounds__(256)
+gemm_batched_kernel(const GemmItem *__restrict__ items)
+{
+    const GemmItem it = items[blockIdx.z];
+    const long long row0 = (long long)blockIdx.x * 64;
+    const int col0 = blockIdx.y * 64;
+    if (row0 >= it.rows || col0 >= it.n) return;
+    __shared__ double2 as[64][17];
+    __shared__ double2 bs[16][64];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int n = it.n;
+    double accr[4][4], acci[4][4], corr[4][4], cori[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { accr[i][j] = 0; acci[i][j] = 0; corr[i][j] = 0; cori[i][j] = 0; }
+    for (int k0 = 0; k0 < n; k0 += 16) {
+        __syncthreads();
+        for (int e = tid; e < 64 * 16; e += 256) {
+            const int r = e % 64, k = e / 64;
+            as[r][k] = (k0 + k < n && row0 + r < it.rows) ? it.A[row0 + r + it.lda * (k0 + k)]
+                                                          : make_double2(0.0, 0.0);
+        }
+        for (int e = tid; e < 16 * 64; e += 256) {
+            const int k = e % 16, c = e / 16;
+            bs[k][c] = (k0 + k < n && col0 + c < n) ? it.B[(k0 + k) + it.ldb * (col0 + c)]
+                                                   : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+        if (it.accurate) {
+            for (int k = 0; k < 16; ++k) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const double2 x = as[ty + 16 * i][k];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const double2 z = bs[k][tx + 16 * j];
+                        acc2(accr[i][j], corr[i][j], x.x, z.x);
+                        acc2(accr[i][j], corr[i][j], -x.y, z.y);
+                        acc2(acci[i][j], cori[i][j], x.x, z.y);
+                        acc2(acci[i][j], cori[i][j], x.y, z.x);
+                    }
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (int k = 0; k < 16; ++k) {
+                double2 x[4], z[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[i] = as[ty + 16 * i][k];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) z[j] = bs[k][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        accr[i][j] = fma(x[i].x, z[j].x, accr[i][j]);
+                        accr[i][j] = fma(-x[i].y, z[j].y, accr[i][j]);
+                        acci[i][j] = fma(x[i].x, z[j].y, acci[i][j]);
+                        acci[i][j] = fma(x[i].y, z[j].x, acci[i][j]);
+                    }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long r = row0 + ty + 16 * i;
+            const int c = col0 + tx + 16 * j;
+            if (r < it.rows && c < n)
+                it.C[r + it.ldc * c] = make_double2(accr[i][j] + corr[i][j], acci[i][j] + cori[i][j]);
+        }
+}
+
+// kappa[i] = ||G_i||_F max_j ||(V0_i)_j||, an estimate of the condition of a
+// warm-start basis relative to G_i (item fields: A = V0_i, lda, n; B holds the
+// squared column norms of G_i as doubles).  One CTA per item.
+__global__ void __launch_bounds__(256)
+v0_kappa_kernel(const GemmItem *__restrict__ items, double *__restrict__ kappa)
+{
+    __shared__ double rg[8], rv[8];
+    const GemmItem it = items[blockIdx.x];
+    const double *gcol2 = (const double *)it.B;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double g = 0.0, vmax = 0.0;
+    for (int j = warp; j < it.n; j += 8) {          // one warp per column, lanes over rows
+        double v = 0.0;
+        for (int i = lane; i < it.n; i += 32) {
+            const double2 a = it.A[i + it.lda * j];
+            v = fma(a.x, a.x, fma(a.y, a.y, v));
+        }
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        vmax = fmax(vmax, v);
+        if (lane == 0) g += gcol2[j];
+    }
+    if (lane == 0) { rg[warp] = g; rv[warp] = vmax; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double gs = 0.0, vm = 0.0;
+        for (int k = 0; k < 8; ++k) { gs += rg[k]; vm = fmax(vm, rv[k]); }
+        kappa[blockIdx.x] = sqrt(gs) * sqrt(vm);
+    }
+}
+
+// Batched copy of column-major blocks: dst_i (rows x n, ldd) <- src_i (lds).
+__global__ void copy_batched_kernel(const GemmItem *__restrict__ items)
+{
+    // item fields reused: A = source (lda), C = destination (ldc), rows, n
+    const GemmItem it = items[blockIdx.y];
+    const long long total = (long long)it.rows * it.n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e % it.rows, c = e / it.rows;
+        it.C[r + it.ldc * c] = it.A[r + it.lda * c];
+    }
+}
+
 // Identity into rows [r0, r0 + n_pad) of an n-column complex64 buffer.
 __global__ void eye32_kernel(float2 *__restrict__ W, long long ld, int r0, int n, int n_pad)
 {
@@ -352,6 +492,35 @@ static size_t inner_smem(bool single)
     return 3 * (single ? sizeof(float2) : sizeof(double2)) * KKMAX * KKMAX;
 }
 
+// Cluster widths of the inner level usable on this device (bit CL set: a
+// cluster of CL CTAs with the inner kernel's shared memory can be resident).
+static int g_cluster_mask = -1;
+
+template <typename TP, typename TU, int CL>
+static cudaError_t setup_cluster(bool single, int *mask)
+{
+    auto k = inner_cluster_kernel<TP, TU, CL>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)inner_smem(single));
+    if (e != cudaSuccess) { cudaGetLastError(); return cudaSuccess; }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = inner_smem(single);
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = CL;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg);
+    if (e != cudaSuccess) { cudaGetLastError(); return cudaSuccess; }
+    if (nclusters > 0) *mask |= CL;
+    return cudaSuccess;
+}
+
 cudaError_t setup_kernels()
 {
     cudaError_t e;
@@ -366,13 +535,66 @@ cudaError_t setup_kernels()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(update_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(2 * sizeof(float2) * KKMAX * KKMAX));
-    return e;
+    if (e != cudaSuccess) return e;
+    if (g_cluster_mask < 0) {
+        int m64 = 0, m32 = 0;
+        const char *env = getenv("GHSVD_INNER_CLUSTER");
+        if (!(env && env[0] == '0')) {
+            setup_cluster<double, double, 2>(false, &m64);
+            setup_cluster<double, double, 4>(false, &m64);
+            setup_cluster<float, float, 2>(true, &m32);
+            setup_cluster<float, float, 4>(true, &m32);
+        }
+        g_cluster_mask = m64 & m32;
+    }
+    return cudaSuccess;
+}
+
+template <typename TP, typename TU, int CL>
+static cudaError_t launch_inner_cluster(const void *partial, const int *slotcol, const InnerArgs &a,
+                                        double2 *zhat, int *pair_flag, unsigned long long *counters,
+                                        int *err, cudaStream_t s, bool single)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.npairs * CL);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = inner_smem(single);
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = CL;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, inner_cluster_kernel<TP, TU, CL>,
+                              (const typename cplx<TP>::t *)partial, slotcol, a, zhat, pair_flag,
+                              counters, err);
 }
 
 cudaError_t launch_inner(const void *partial, bool single, const int *slotcol, const InnerArgs &a,
                          double2 *zhat, int *pair_flag, unsigned long long *counters, int *err,
                          cudaStream_t s)
 {
+    // FP64 sweeps: spread each block pivot over a cluster of 4 (or 2) SMs
+    // when the step's pairs leave SMs idle (the complex64 sweeps are bound by
+    // the FP64 parameter chain, which a cluster does not shorten)
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int mask = (g_cluster_mask < 0 || single) ? 0 : g_cluster_mask;
+    if ((mask & 4) && a.npairs * 4 <= sms) {
+        return single ? launch_inner_cluster<float, float, 4>(partial, slotcol, a, zhat, pair_flag,
+                                                              counters, err, s, true)
+                      : launch_inner_cluster<double, double, 4>(partial, slotcol, a, zhat, pair_flag,
+                                                                counters, err, s, false);
+    }
+    if ((mask & 2) && a.npairs * 2 <= sms) {
+        return single ? launch_inner_cluster<float, float, 2>(partial, slotcol, a, zhat, pair_flag,
+                                                              counters, err, s, true)
+                      : launch_inner_cluster<double, double, 2>(partial, slotcol, a, zhat, pair_flag,
+                                                                counters, err, s, false);
+    }
     if (single)
         inner_kernel<float, float><<<a.npairs, 1024, inner_smem(true), s>>>(
             (const float2 *)partial, slotcol, a, zhat, pair_flag, counters, err);
@@ -424,6 +646,27 @@ cudaError_t launch_gemm(const double2 *A, long long lda, int rows, const void *B
         gemm_kernel<float2><<<grid, 256, 0, s>>>(A, lda, (const float2 *)B, ldb, C, ldc, n);
     else
         gemm_kernel<double2><<<grid, 256, 0, s>>>(A, lda, (const double2 *)B, ldb, C, ldc, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_batched(const GemmItem *items, int count, long long max_rows, int max_n,
+                                cudaStream_t s)
+{
+    dim3 grid((unsigned)((max_rows + 63) / 64), (unsigned)((max_n + 63) / 64), (unsigned)count);
+    gemm_batched_kernel<<<grid, 256, 0, s>>>(items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_v0_kappa(const GemmItem *items, int count, double *kappa, cudaStream_t s)
+{
+    v0_kappa_kernel<<<count, 256, 0, s>>>(items, kappa);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_batched(const GemmItem *items, int count, cudaStream_t s)
+{
+    dim3 grid(256, (unsigned)count);
+    copy_batched_kernel<<<grid, 256, 0, s>>>(items);
     return cudaGetLastError();
 }
 

@@ -186,8 +186,11 @@ unsigned grid_for(long long n, int threads = 256, int cap = 4096)
 
 // C = X^* X for X (rows x n, column-major, ld), C n x n column-major (FP64).
 __global__ void __launch_bounds__(256)
-zgram_full(const double2 *__restrict__ X, long long ld, int rows, int n, double2 *__restrict__ C)
+zgram_full(const double2 *__restrict__ Xs, long long ld, int rows, int n, double2 *__restrict__ Cs)
 {
+    // item blockIdx.z: X = Xs + z ld n, C = Cs + z n n
+    const double2 *X = Xs + (long long)blockIdx.z * ld * n;
+    double2 *C = Cs + (long long)blockIdx.z * n * n;
     __shared__ double2 xs[16][65];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
@@ -599,52 +602,47 @@ ghsvd_status ghsvd_s_orthonormalize(int count, int64_t p, int64_t n, const void 
     for (int i = 0; i < count; ++i)
         if (!G[i] || !V0[i] || ldg[i] < p || ldv0[i] < n) return GHSVD_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    // per matrix: X = G V0 (p x n), C = X^* X = L L^*, V0 <- V0 (L^{-1})^*
-    const long long p_pad = (p + 63) / 64 * 64, n_pad = (n + 63) / 64 * 64;
-    double2 *Gp = nullptr, *X = nullptr, *C = nullptr, *Xb = nullptr, *B = nullptr, *Vp = nullptr;
+    // for every pair: X = G V0 (p x n), C = X^* X = L L^*, V0 <- V0 (L^{-1})^*;
+    // each stage is one batched launch over all pairs
+    double2 *X = nullptr, *C = nullptr, *Xb = nullptr, *B = nullptr, *Y = nullptr;
+    hz::GemmItem *items = nullptr;
     int *bad = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&Gp, 16 * p_pad * n, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&X, 16 * p_pad * n, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&C, 16LL * count * n * n, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&Xb, 16LL * count * n * n, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&B, 16LL * count * n * n, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&Vp, 16 * n_pad * n, st);
+    const long long pn = p * n, nn = n * n;
+    cudaError_t e = cudaMallocAsync((void **)&X, 16LL * count * pn, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&C, 16LL * count * nn, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&Xb, 16LL * count * nn, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&B, 16LL * count * nn, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&Y, 16LL * count * nn, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&items, sizeof(hz::GemmItem) * count, st);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&bad, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(Gp, 0, 16 * p_pad * n, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(Vp, 0, 16 * n_pad * n, st);
-    const dim3 ggrid((unsigned)((n + 63) / 64), (unsigned)((n + 63) / 64));
-    // Grams (zero-padded copies so that the FP64 GEMM sees whole 64-row tiles)
-    for (int i = 0; i < count && e == cudaSuccess; ++i) {
-        e = cudaMemcpy2DAsync(Gp, 16 * p_pad, G[i], 16 * ldg[i], 16 * p, n, cudaMemcpyDeviceToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(Vp, 16 * n_pad, V0[i], 16 * ldv0[i], 16 * n, n,
-                                  cudaMemcpyDeviceToDevice, st);
-        if (e == cudaSuccess) e = hz::launch_gemm(Gp, p_pad, (int)p_pad, Vp, false, n_pad, X, p_pad, (int)n, st);
-        if (e == cudaSuccess) {
-            zgram_full<<<ggrid, 256, 0, st>>>(X, p_pad, (int)p, (int)n, C + (long long)i * n * n);
-            e = cudaGetLastError();
-        }
-    }
-    // all Cholesky factorizations and inverses at once, one CTA each
+    std::vector<hz::GemmItem> it(count);
+    for (int i = 0; i < count; ++i)
+        it[i] = {(const double2 *)G[i], ldg[i], p, (const double2 *)V0[i], ldv0[i], X + i * pn, p, (int)n, 0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(items, it.data(), sizeof(hz::GemmItem) * count, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = hz::launch_gemm_batched(items, count, p, (int)n, st);
     if (e == cudaSuccess) {
+        dim3 grid((unsigned)((n + 63) / 64), (unsigned)((n + 63) / 64), (unsigned)count);
+        zgram_full<<<grid, 256, 0, st>>>(X, p, (int)p, (int)n, C);
         chol_inv<<<count, 1024, 0, st>>>(C, (int)n, Xb, B, bad);
         e = cudaGetLastError();
     }
-    // V0 <- V0 B
-    for (int i = 0; i < count && e == cudaSuccess; ++i) {
-        e = cudaMemcpy2DAsync(Vp, 16 * n_pad, V0[i], 16 * ldv0[i], 16 * n, n, cudaMemcpyDeviceToDevice, st);
-        if (e == cudaSuccess)
-            e = hz::launch_gemm(Vp, n_pad, (int)n_pad, B + (long long)i * n * n, false, n, X, n_pad,
-                                (int)n, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(V0[i], 16 * ldv0[i], X, 16 * n_pad, 16 * n, n,
-                                  cudaMemcpyDeviceToDevice, st);
-    }
+    for (int i = 0; i < count; ++i)
+        it[i] = {(const double2 *)V0[i], ldv0[i], n, B + i * nn, n, Y + i * nn, n, (int)n, 0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(items, it.data(), sizeof(hz::GemmItem) * count, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = hz::launch_gemm_batched(items, count, n, (int)n, st);
+    for (int i = 0; i < count; ++i)
+        it[i] = {Y + i * nn, n, n, nullptr, 0, (double2 *)V0[i], ldv0[i], (int)n, 0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(items, it.data(), sizeof(hz::GemmItem) * count, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = hz::launch_copy_batched(items, count, st);
     int hbad = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaFreeAsync(Gp, st); cudaFreeAsync(X, st); cudaFreeAsync(C, st); cudaFreeAsync(Xb, st);
-    cudaFreeAsync(B, st); cudaFreeAsync(Vp, st); cudaFreeAsync(bad, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(X, st); cudaFreeAsync(C, st); cudaFreeAsync(Xb, st); cudaFreeAsync(B, st);
+    cudaFreeAsync(Y, st); cudaFreeAsync(items, st); cudaFreeAsync(bad, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return st_of(e);
     return hbad ? GHSVD_ERR_RANK_DEFICIENT : GHSVD_OK;
