@@ -5,8 +5,9 @@ tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
 import this package.  It shares no code with the GPU library.
 
 The arithmetic lives in ``hz_oracle.c`` (plain C, ``double complex``), which
-follows arXiv 1907.08560 Section 6 step by step; this module only compiles it
-and marshals numpy arrays (column-major complex128) to it.
+follows arXiv 1907.08560 Section 6 step by step, and ``phase24_oracle.c``
+(Phase 2 of Section 5 and Phase 4 of Section 7); this module only compiles
+them and marshals numpy arrays (column-major complex128) to them.
 """
 from __future__ import annotations
 
@@ -18,19 +19,21 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hz_oracle.c")
+_SRC24 = os.path.join(_HERE, "phase24_oracle.c")
 _LIB = os.path.join(_HERE, "libhz_oracle.so")
 
 _lib = None
 
 
 def build(force: bool = False, out: str | None = None, defines: tuple[str, ...] = ()) -> str:
-    """Compile hz_oracle.c with gcc (-O2, OpenMP) into a shared library."""
+    """Compile the oracle sources with gcc (-O2, OpenMP) into a shared library."""
     out = out or _LIB
-    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC24))
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
         return out
     cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=gnu11",
            "-fno-fast-math", "-ffp-contract=off", *[f"-D{d}" for d in defines],
-           _SRC, "-o", out, "-lm"]
+           _SRC, _SRC24, "-o", out, "-lm"]
     subprocess.run(cmd, check=True)
     return out
 
@@ -63,6 +66,14 @@ def _bind(lib):
     lib.hzo_rank_check.argtypes = [c_long, c_long, vp, c_long, vp, c_long, ctypes.POINTER(c_double)]
     lib.hzo_pivot2.restype = c_int
     lib.hzo_pivot2.argtypes = [vp, c_double, c_int, vp, ctypes.POINTER(c_int)]
+    lib.p24_jqr.restype = c_int
+    lib.p24_jqr.argtypes = [c_long, c_long, vp, c_long, vp, vp, ctypes.POINTER(c_long)]
+    lib.p24_qr.restype = c_int
+    lib.p24_qr.argtypes = [c_long, c_long, vp, c_long]
+    lib.p24_lu_complete.restype = c_int
+    lib.p24_lu_complete.argtypes = [c_long, vp, c_long, vp, vp]
+    lib.p24_inverse.restype = c_int
+    lib.p24_inverse.argtypes = [c_long, vp, c_long, vp, vp, vp, c_long]
     return lib
 
 
@@ -275,3 +286,97 @@ def rr_table(N, lib=None):
 
 def max_threads(lib=None):
     return (lib or load()).hzo_max_threads()
+
+
+# --------------------------------------------------------------------------
+# Phase 2 (Section 5) and Phase 4 (Section 7).
+# --------------------------------------------------------------------------
+
+def jqr(F, J=None, lib=None):
+    """The hyperbolic QR of Section 5 (p24_jqr).
+
+    Returns dict(R = the n x n block upper triangular factor, J = its
+    signature (n entries), perm (F~[:, perm] = F~ P2), n2x2, status, and the
+    whole transformed m x n factor ``full`` with its row-permuted ``J_full``)."""
+    lib = lib or load()
+    F = _fortran(F)
+    m, n = F.shape
+    Jv = np.ones(m, dtype=np.int8) if J is None else _signs(J, m).copy()
+    perm = np.zeros(n, dtype=np.int64)
+    n2 = ctypes.c_long(0)
+    rc = lib.p24_jqr(m, n, _ptr(F), m, _ptr(Jv), _ptr(perm), ctypes.byref(n2))
+    return dict(R=np.asfortranarray(F[:n, :]), J=Jv[:n].copy(), perm=perm, n2x2=n2.value,
+                status=rc, full=F, J_full=Jv)
+
+
+def qr(G, lib=None):
+    """Householder QR of G (p24_qr): the n x n upper triangular R with G^*G = R^*R."""
+    lib = lib or load()
+    G = _fortran(G)
+    p, n = G.shape
+    rc = lib.p24_qr(p, n, _ptr(G), p)
+    if rc != 0:
+        raise RuntimeError(f"p24_qr failed: {rc}")
+    return np.asfortranarray(G[:n, :])
+
+
+def urv(F, G, J=None, lib=None):
+    """Phase 2: the square pencil (R_F, J', R_G) of the tall (F~, J~, G~):
+    R_F from the JQR of F~, R_G from the QR of G~ P2 (Section 5).
+    Returns dict(F, J, G, perm, n2x2, status)."""
+    out = jqr(F, J, lib=lib)
+    if out["status"] != 0:
+        return dict(status=out["status"])
+    Gp = np.asarray(G)[:, out["perm"]]
+    return dict(F=out["R"], J=out["J"], G=qr(Gp, lib=lib), perm=out["perm"],
+                n2x2=out["n2x2"], status=0)
+
+
+def lu_complete(A, lib=None):
+    """P A Q = L U by complete pivoting (p24_lu_complete); returns (LU, rowp, colp, status)."""
+    lib = lib or load()
+    A = _fortran(A)
+    n = A.shape[0]
+    rowp = np.zeros(n, dtype=np.int64)
+    colp = np.zeros(n, dtype=np.int64)
+    rc = lib.p24_lu_complete(n, _ptr(A), n, _ptr(rowp), _ptr(colp))
+    return A, rowp, colp, rc
+
+
+def inverse(Z, lib=None):
+    """X = Z^{-1} by complete pivoting and Z X = I (Section 7)."""
+    lib = lib or load()
+    LU, rowp, colp, rc = lu_complete(Z, lib=lib)
+    if rc != 0:
+        raise RuntimeError(f"p24_lu_complete failed: {rc}")
+    n = LU.shape[0]
+    X = np.zeros((n, n), dtype=np.complex128, order="F")
+    rc = lib.p24_inverse(n, _ptr(LU), n, _ptr(rowp), _ptr(colp), _ptr(X), n)
+    if rc != 0:
+        raise RuntimeError(f"p24_inverse failed: {rc}")
+    return X
+
+
+def ghsvd(F, G, J, Fp, Gp, Zp, lib=None):
+    """Phase 4 and the errors of eq. 7.1 for converged factors F' = F Z',
+    G' = G Z' (Section 6.1.7 outputs, Section 7):
+    Sigma_F' = |f'_j^* J f'_j|^{1/2}, Sigma_G' = ||g'_j||,
+    Sigma = (Sigma_F'^2 + Sigma_G'^2)^{1/2}, Z = Z' Sigma^{-1}, X = Z^{-1},
+    U = F' Sigma_F'^{-1}, V = G' Sigma_G'^{-1}, Sigma_F = Sigma_F' / Sigma,
+    Sigma_G = Sigma_G' / Sigma, and
+    err_F = ||F - U Sigma_F X||_F / ||F||_F, err_G = ||G - V Sigma_G X||_F / ||G||_F."""
+    F = np.asarray(F); G = np.asarray(G)
+    Fp = np.asarray(Fp); Gp = np.asarray(Gp); Zp = np.asarray(Zp)
+    m = F.shape[0]
+    Jd = np.ones(m) if J is None else np.asarray(J, dtype=np.float64)
+    sfp = np.sqrt(np.abs(np.einsum("ij,i,ij->j", Fp.conj(), Jd, Fp).real))
+    sgp = np.sqrt(np.einsum("ij,ij->j", Gp.conj(), Gp).real)
+    sig = np.sqrt(sfp ** 2 + sgp ** 2)
+    Z = Zp / sig[None, :]
+    X = inverse(Z, lib=lib)
+    U = Fp / sfp[None, :]
+    V = Gp / sgp[None, :]
+    SF, SG = sfp / sig, sgp / sig
+    errF = np.linalg.norm(F - (U * SF[None, :]) @ X) / np.linalg.norm(F)
+    errG = np.linalg.norm(G - (V * SG[None, :]) @ X) / np.linalg.norm(G)
+    return dict(X=X, Z=Z, U=U, V=V, sigma_f=SF, sigma_g=SG, sigma=sig, err_F=errF, err_G=errG)

@@ -1,10 +1,11 @@
 """The pins are sharp: plant a plausible mistake in a copy of the oracle and
 check that at least one pin fails.
 
-Each mutation is a one-line textual change of ``oracle/hz_oracle.c`` (a
-dropped term, a wrong sign, a wrong index, a transposed operand), compiled
-to a temporary library on the CPU.  The battery below is a subset of the
-pins of test_oracle_pins.py, re-run against the mutant.
+Each mutation is a one-line textual change of ``oracle/hz_oracle.c`` or
+``oracle/phase24_oracle.c`` (a dropped term, a wrong sign, a wrong index, a
+transposed operand), compiled to a temporary library on the CPU.  The
+batteries below are subsets of the pins of test_oracle_pins.py and
+test_oracle_phase24.py, re-run against the mutant.
 """
 import json
 import os
@@ -19,6 +20,7 @@ from synth import pencils as P
 from conftest import rel_err
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "hz_oracle.c")
+SRC24 = os.path.join(os.path.dirname(oracle.__file__), "phase24_oracle.c")
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "tiny_pencils.json")
 
 MUTATIONS = {
@@ -42,14 +44,40 @@ MUTATIONS = {
 }
 
 
-def build_mutant(tmp_path, name):
-    old, new = MUTATIONS[name]
-    src = open(SRC).read()
+MUTATIONS24 = {
+    "jqr_tau_sign_flipped": ("const double tau = -1.0 / (h + rh * r1 * (double)J[k]);",
+                             "const double tau = 1.0 / (h + rh * r1 * (double)J[k]);"),
+    "jqr_no_row_pivoting": ("if (J[k] != sg) {                                     /* row pivoting */",
+                            "if (0) {"),
+    "jqr_jdot_not_conjugated": ("s += (double)J[i] * (conj(a[i]) * b[i]);",
+                                "s += (double)J[i] * (a[i] * b[i]);"),
+    "jqr_c1_phase_dropped": ("const zc c1 = rh * eid;", "const zc c1 = rh;"),
+    "jqr_2x2_block_times_R_not_Rstar": ("f2[i] = x * conj(R21) + y * conj(R22);",
+                                        "f2[i] = x * R21 + y * R22;"),
+    "jqr_reflector_skips_last_row": ("for (long i = k; i < m; ++i) g[i] += t * s[i];",
+                                     "for (long i = k; i < m - 1; ++i) g[i] += t * s[i];"),
+    "jqr_column_swap_not_recorded": ("long t = perm[k]; perm[k] = perm[jmax]; perm[jmax] = t;",
+                                     "long t = perm[k]; (void)t;"),
+    "qr_beta_doubled": ("const double beta = 1.0 / (nrm * (nrm + ax));",
+                        "const double beta = 2.0 / (nrm * (nrm + ax));"),
+    "qr_v_not_conjugated": ("for (long i = k; i < p; ++i) d += conj(v[i]) * g[i];",
+                            "for (long i = k; i < p; ++i) d += v[i] * g[i];"),
+    "lu_column_exchange_not_undone": ("zc t = x[k]; x[k] = x[colp[k]]; x[colp[k]] = t;",
+                                      "(void)0;"),
+    "lu_multiplier_not_divided": ("for (long i = k + 1; i < n; ++i) A[i + lda * k] /= piv;",
+                                  "for (long i = k + 1; i < n; ++i) A[i + lda * k] *= 1.0;"),
+}
+
+
+def build_mutant(tmp_path, name, table=None, src_path=SRC):
+    old, new = (table or MUTATIONS)[name]
+    src = open(src_path).read()
     assert src.count(old) == 1, f"mutation anchor not unique: {old}"
     path = tmp_path / f"{name}.c"
     path.write_text(src.replace(old, new))
+    other = SRC24 if src_path == SRC else SRC
     so = tmp_path / f"lib{name}.so"
-    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=gnu11", str(path),
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=gnu11", str(path), other,
                     "-o", str(so), "-lm"], check=True)
     return oracle.load(str(so))
 
@@ -117,8 +145,59 @@ def _solve(lib, F, G, J, method, kw):
     return out
 
 
+def battery24(lib):
+    """Phase 2 / Phase 4 pins (Sections 5 and 7); AssertionError on the first violated one."""
+    rng = np.random.default_rng(3)
+
+    def herm(F, J):
+        return F.conj().T @ (np.asarray(J, dtype=np.float64)[:, None] * F)
+
+    # J = I: the hyperbolic QR is the QR with column pivoting
+    F = (rng.standard_normal((30, 12)) + 1j * rng.standard_normal((30, 12))) * \
+        10.0 ** rng.uniform(-2, 2, 12)[None, :]
+    out = oracle.jqr(F, np.ones(30, dtype=np.int8), lib=lib)
+    assert out["status"] == 0
+    Rn = np.linalg.qr(F[:, out["perm"]], mode="r")
+    assert np.allclose(np.abs(np.diagonal(out["R"])), np.abs(np.diagonal(Rn)), rtol=1e-12)
+    assert np.all(np.diff(np.abs(np.diagonal(out["R"]))) <= 1e-12 * np.abs(out["R"]).max())
+    # QR of G against numpy
+    G = rng.standard_normal((20, 9)) + 1j * rng.standard_normal((20, 9))
+    R = oracle.qr(G, lib=lib)
+    Rn = np.linalg.qr(G, mode="r")
+    ph = np.diagonal(R) / np.diagonal(Rn)
+    assert np.allclose(R, ph[:, None] * Rn, atol=1e-13 * np.abs(Rn).max())
+    # the Hermitian form and the inertia on indefinite factors (with 2x2 pivots)
+    n2 = 0
+    for t in range(12):
+        J = np.where(rng.random(20) < 0.5, -1, 1).astype(np.int8)
+        F = rng.standard_normal((20, 12)) + 1j * rng.standard_normal((20, 12))
+        out = oracle.jqr(F, J, lib=lib)
+        assert out["status"] == 0
+        H0 = herm(F[:, out["perm"]], J)
+        assert np.max(np.abs(herm(out["R"], out["J"]) - H0)) <= 1e-13 * np.linalg.norm(F) ** 2
+        assert np.all(np.tril(out["R"], -2) == 0)
+        assert np.count_nonzero(out["J"] < 0) == np.count_nonzero(np.linalg.eigvalsh(herm(F, J)) < 0)
+        n2 += out["n2x2"]
+    assert n2 > 0
+    # X = Z^{-1}
+    Z = rng.standard_normal((15, 15)) + 1j * rng.standard_normal((15, 15))
+    X = oracle.inverse(Z, lib=lib)
+    assert np.max(np.abs(X - np.linalg.inv(Z))) <= 1e-10 * np.abs(X).max()
+
+
 def test_battery_passes_on_the_real_oracle():
     battery(oracle.load())
+
+
+def test_battery24_passes_on_the_real_oracle():
+    battery24(oracle.load())
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS24))
+def test_planted_phase24_mistake_is_caught(tmp_path, name):
+    lib = build_mutant(tmp_path, name, MUTATIONS24, SRC24)
+    with pytest.raises((AssertionError, RuntimeError, ValueError, np.linalg.LinAlgError)):
+        battery24(lib)
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
