@@ -393,6 +393,12 @@ def main():
     ap.add_argument("--mixed-steps", type=int, default=1,
                     help="timed solves of the mixed-precision schedule (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--split-steps", type=int, default=1,
+                    help="timed solves with the block update on the bf16 tensor cores (0: skip)")
+    ap.add_argument("--phase2-steps", type=int, default=1,
+                    help="timed solves with Phase 2 shortening first (0: skip)")
+    ap.add_argument("--no-phase4", dest="phase4", action="store_false",
+                    help="skip X = Z^{-1} and the errors of eq. 7.1")
     ap.add_argument("--workload", choices=["pencil", "batched", "warmstart"], default="pencil")
     ap.add_argument("--family-n", type=int, default=256)
     ap.add_argument("--train", type=int, default=1500)
@@ -529,13 +535,46 @@ def main():
                "h2d_bytes_per_step": (M * N + P * N) * 16 + M,
                "d2h_bytes_per_step": N * 8 + N * N * 16}
 
-    # speedup of the mixed-precision schedule over the FP64 solve at equal
-    # eigenvalue error (only alongside the default FP64 measurement)
-    mixed = None
-    if args.precision == "fp64" and args.mixed_steps > 0:
+    # the FP64 reference of this pencil for the variants below: eigenvalues,
+    # converged columns and the per-eigenvalue tolerance (cond by construction:
+    # F 1e6, G 10^5; the hyperbolic amplification a_j of the converged columns)
+    ref64 = None
+    if args.precision == "fp64" and (args.mixed_steps > 0 or args.phase2_steps > 0 or args.phase4 or
+                                     args.split_steps > 0):
         lam64, _, _, _ = solver.solve(Fd, Gd, Jd, stream=stream)
         Fp64, _, _ = solver.factors(M, P, N)
         lam64 = lam64.cpu().numpy()
+        F64 = Fp64.cpu().numpy()
+        Jf = J.astype(np.float64)
+        amp = (np.einsum("ij,ij->j", F64.conj(), F64).real /
+               np.abs(np.einsum("ij,i,ij->j", F64.conj(), Jf, F64).real))
+        order = np.argsort(lam64)
+        ref64 = dict(lam=lam64[order], tol=1e-12 * max(1.0, (1e6 + 10 ** 5) / 1e3) * amp[order])
+        del F64, Fp64
+
+    def eig_vs_fp64(lam):
+        err = np.abs(np.sort(lam.cpu().numpy()) - ref64["lam"]) / np.abs(ref64["lam"])
+        return float(err.max()), float((err / ref64["tol"]).max())
+
+    # Phase 4 (X = Z^{-1}) and the errors of eq. 7.1 of the FP64 solve above
+    phase4 = None
+    if ref64 is not None and args.phase4:
+        torch.cuda.synchronize()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        sf, sg, X = solver.phase4(N, stream=stream)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        ef, eg = solver.decomposition_errors(Fd, Gd, X, stream=stream)
+        phase4 = {"ms": q0.elapsed_time(q1), "err_F_eq7_1": ef, "err_G_eq7_1": eg,
+                  "what": "Sigma_F, Sigma_G and X = Z^{-1} by complete pivoting (n = 2048)"}
+        del sf, sg, X
+
+    # speedup of the mixed-precision schedule over the FP64 solve at equal
+    # eigenvalue error (only alongside the default FP64 measurement)
+    mixed = None
+    if ref64 is not None and args.mixed_steps > 0:
         msolver = ghsvd.Solver(local, block_width=W_BLOCK, precision=ghsvd.GHSVD_PRECISION_MIXED,
                                max_sweeps=args.max_sweeps, mixed_max_sweeps=60)
         msolver.solve(Fd, Gd, Jd, stream=stream)          # warm-up
@@ -552,24 +591,84 @@ def main():
         torch.cuda.synchronize()
         mixed_ms = allreduce(m0.elapsed_time(m1), dist.ReduceOp.MAX if dist else None)
         ms_stats = msolver.stats()
-        # per-eigenvalue tolerance (cond by construction: F 1e6, G 10^5; the
-        # hyperbolic amplification a_j from the FP64 solve's converged columns)
-        F64 = Fp64.cpu().numpy()
-        Jf = J.astype(np.float64)
-        amp = (np.einsum("ij,ij->j", F64.conj(), F64).real /
-               np.abs(np.einsum("ij,i,ij->j", F64.conj(), Jf, F64).real))
-        order = np.argsort(lam64)
-        tol = 1e-12 * max(1.0, (1e6 + 10 ** 5) / 1e3) * amp[order]
-        err = np.abs(np.sort(lam_m.cpu().numpy()) - lam64[order]) / np.abs(lam64[order])
+        emax, eratio = eig_vs_fp64(lam_m)
         mvalue = world * args.mixed_steps / (mixed_ms / 1e3)
         mixed = {"value": mvalue, "unit": "solves/s", "ms_per_step": mixed_ms / args.mixed_steps,
                  "speedup_vs_fp64": mvalue / value, "status": mst,
                  "sweeps_complex64": ms_stats["sweeps_low"],
                  "sweeps_fp64": ms_stats["sweeps"] - ms_stats["sweeps_low"],
                  "rounds_complex64": ms_stats["rounds_low"],
-                 "eig_rel_diff_vs_fp64_max": float(err.max()),
-                 "eig_rel_diff_over_tol_max": float((err / tol).max())}
+                 "eig_rel_diff_vs_fp64_max": emax,
+                 "eig_rel_diff_over_tol_max": eratio}
         msolver.close()
+
+    # Phase 2 first (the square factors of the (J, I) URV factorization), then
+    # the FP64 iteration on them; eigenvectors mapped back to the tall pencil
+    shortened = None
+    if ref64 is not None and args.phase2_steps > 0:
+        ssolver = ghsvd.Solver(local, block_width=W_BLOCK, max_sweeps=args.max_sweeps, shorten=1)
+        ssolver.solve(Fd, Gd, Jd, stream=stream)          # warm-up
+        torch.cuda.synchronize()
+        barrier()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        sst, ph2 = [], 0.0
+        for _ in range(args.phase2_steps):
+            lam_s, _, sw_s, st_s = ssolver.solve(Fd, Gd, Jd, stream=stream)
+            sst.append(st_s)
+            ph2 += ssolver.stats()["ms_phase2"]
+        s1.record(stream)
+        torch.cuda.synchronize()
+        sh_ms = allreduce(s0.elapsed_time(s1), dist.ReduceOp.MAX if dist else None)
+        sstats = ssolver.stats()
+        emax, eratio = eig_vs_fp64(lam_s)
+        svalue = world * args.phase2_steps / (sh_ms / 1e3)
+        shortened = {"value": svalue, "unit": "solves/s", "ms_per_step": sh_ms / args.phase2_steps,
+                     "ms_phase2": ph2 / args.phase2_steps, "n2x2_pivots": sstats["n2x2"],
+                     "sweeps": sstats["sweeps"], "speedup_vs_tall_fp64": svalue / value,
+                     "status": sst, "eig_rel_diff_vs_fp64_max": emax,
+                     "eig_rel_diff_over_tol_max": eratio}
+        ssolver.close()
+
+    # the FP64 solve with the block update on the bf16 tensor cores (FP64
+    # accuracy by exact integer slices); same pencil, same stopping rule
+    split = None
+    if ref64 is not None and args.split_steps > 0:
+        psolver = ghsvd.Solver(local, block_width=W_BLOCK, max_sweeps=args.max_sweeps, timing=1,
+                               update_engine=ghsvd.GHSVD_UPDATE_SPLIT_BF16)
+        psolver.solve(Fd, Gd, Jd, stream=stream)          # warm-up
+        torch.cuda.synchronize()
+        barrier()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        pst, pupd, pl = [], 0.0, 0
+        for _ in range(args.split_steps):
+            lam_p, _, sw_p, st_p = psolver.solve(Fd, Gd, Jd, stream=stream)
+            pst.append(st_p)
+            ps = psolver.stats()
+            pupd += ps["ms_update"]
+            pl += ps["launches_update"]
+        p1.record(stream)
+        torch.cuda.synchronize()
+        sp_ms = allreduce(p0.elapsed_time(p1), dist.ReduceOp.MAX if dist else None)
+        emax, eratio = eig_vs_fp64(lam_p)
+        pvalue = world * args.split_steps / (sp_ms / 1e3)
+        upd_launch_ms = pupd / max(pl, 1)
+        mma_flops = 36 * update_flops_per_launch()      # slice products actually issued (K = 128)
+        bf16_peak = measured_bf16_peak()
+        split = {"value": pvalue, "unit": "solves/s", "ms_per_step": sp_ms / args.split_steps,
+                 "speedup_vs_fp64_update": pvalue / value, "status": pst,
+                 "sweeps": psolver.stats()["sweeps"],
+                 "update_ms_per_launch": upd_launch_ms,
+                 "update_fp64_equivalent_tflops": update_flops_per_launch() / (upd_launch_ms * 1e-3) / 1e12,
+                 "update_bf16_tflops": mma_flops / (upd_launch_ms * 1e-3) / 1e12,
+                 "bf16_peak_measured": bf16_peak,
+                 "update_bf16_frac_of_measured_peak":
+                     (mma_flops / (upd_launch_ms * 1e-3) / 1e12) / bf16_peak if bf16_peak else None,
+                 "eig_rel_diff_vs_fp64_max": emax, "eig_rel_diff_over_tol_max": eratio}
+        psolver.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -587,6 +686,7 @@ def main():
                            "status": status, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (235 MB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed_precision": mixed,
+                "phase2_shortened": shortened, "phase4": phase4, "split_bf16_update": split,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -601,6 +701,15 @@ def solver_host(ghsvd, solver, Fpin, Gpin, Jpin, lam_pin, V_pin):
                              Gpin.data_ptr(), P, lam_pin.data_ptr(), V_pin.data_ptr(), N,
                              ctypes.byref(sweeps), None)
     return s
+
+
+def measured_bf16_peak():
+    """Dense bf16 TFLOP/s measured on this machine's GPUs (burst), if recorded."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def measure_fp64_peak(device):

@@ -47,8 +47,11 @@ typedef enum {
     GHSVD_ERR_NOT_CONVERGED = 4,   /* max_sweeps reached; outputs still written */
     GHSVD_ERR_CUDA = 5,            /* a CUDA runtime error                      */
     GHSVD_ERR_NOMEM = 6,           /* device allocation failed                  */
-    GHSVD_ERR_SCRATCH_TOO_SMALL = 7 /* ghsvd_solve_noalloc: the problem does not
+    GHSVD_ERR_SCRATCH_TOO_SMALL = 7, /* ghsvd_solve_noalloc: the problem does not
                                       fit GHSVD_NOALLOC_SCRATCH_BYTES          */
+    GHSVD_ERR_BREAKDOWN = 8        /* Phase 2: the hyperbolic QR met a J-isotropic
+                                      nonzero pivot column, or no row whose sign
+                                      matches its J-norm (Section 5.3)        */
 } ghsvd_status;
 
 /* Precision schedules. */
@@ -58,6 +61,14 @@ typedef enum {
                                       FP64 factors by an FP64 product, then FP64
                                       finishing sweeps; the 2x2 parameters,
                                       J-norms and the stopping test are FP64  */
+
+/* Engines of the FP64 block update (Section 6.4.3). */
+#define GHSVD_UPDATE_FP64 0        /* FP64 FMA on the CUDA cores                   */
+#define GHSVD_UPDATE_SPLIT_BF16 1  /* the same product with FP64 accuracy on the bf16
+                                      tensor cores: the FP64 operands are cut into
+                                      8 exact 7-bit integer slices, the slice
+                                      products accumulate exactly in FP32 and are
+                                      combined exactly in 64-bit integers         */
 
 typedef struct {
     int block_width;     /* w: maximal block-column width, 1..32 (Section 6.4.1);
@@ -77,6 +88,16 @@ typedef struct {
     int gram_chunk;      /* rows per Gram work unit; 0 = automatic            */
     int timing;          /* 1: time every step kernel with CUDA events on the
                             solve's stream (ghsvd_stats.ms_*); 0 (default): off */
+    int shorten;         /* 1: Phase 2 first (Section 5, see ghsvd_urv): the
+                            iteration runs on the square factors; lambda is
+                            that of the tall pencil and V is returned in the
+                            caller's column order (rows permuted back by P2).
+                            Not with a warm start.  0 (default): the tall
+                            factors.  ghsvd_solve_batched and
+                            ghsvd_solve_noalloc ignore it.                    */
+    int update_engine;   /* GHSVD_UPDATE_FP64 (default) or GHSVD_UPDATE_SPLIT_BF16
+                            for the FP64 sweeps of ghsvd_solve; the batched and
+                            the no-allocation solves use GHSVD_UPDATE_FP64    */
 } ghsvd_opts;
 
 /* Per-solve statistics (Section 6.4.3, "Completing a sweep"). */
@@ -93,6 +114,8 @@ typedef struct {
     long long launches_gram, launches_inner, launches_update;
     double ms_gram, ms_inner, ms_update;   /* summed device time (timing = 1)     */
     int rounds_low;                /* complex64 rounds (mixed schedule)          */
+    double ms_phase2;              /* wall time of Phase 2 in the solve (shorten) */
+    int n2x2;                      /* 2x2 pivots of that Phase 2                 */
 } ghsvd_stats;
 
 /* Fill *opts with the defaults listed above. */
@@ -292,6 +315,76 @@ ghsvd_status ghsvd_solve_noalloc(int64_t m, int64_t p, int64_t n,
                                  const void *F, int64_t ldf, const int8_t *J, int64_t n_plus,
                                  const void *G, int64_t ldg, double *lambda, void *V, int64_t ldv,
                                  const ghsvd_opts *opts, int *sweeps, void *stream);
+
+/*
+ * Phase 2 (Section 5): the (J, I) URV shortening of the tall pencil
+ * (F~, J~, G~) to a square one (F, J, G) with the same eigenvalues.
+ *   P1 F~ P2 = Q_F [F; 0] by the hyperbolic QR with the diagonal and the
+ *   Bunch-Kaufman partial pivoting of Section 5.2 (alpha = (1 + sqrt 17)/8),
+ *   hyperbolic Householder reflectors (Theorem 5.1, Section 5.3) and 2x2
+ *   pivots through a Jacobi rotation; G~ P2 = Q_G G by the Householder QR.
+ *   Then P2^T F~^* J~ F~ P2 = F^* J F and P2^T G~^* G~ P2 = G^* G, so the
+ *   pencils have the same eigenvalues and the eigenvectors of the tall one
+ *   are Z~ = P2 Z (Section 5).
+ *   m, p, n, F~/ldf, J~/n_plus, G~/ldg  as for ghsvd_solve; F~, G~ and a
+ *             non-NULL J~ in device memory, read only.
+ *   Fs, ldfs  device, complex128 n x n (ldfs >= n): F, block upper
+ *             triangular with diagonal blocks of order 1 or 2.
+ *   Js        device, n int8: J, the leading n signs of the row-permuted J~.
+ *   Gs, ldgs  device, complex128 n x n (ldgs >= n): G, upper triangular.
+ *   perm      device, n int64, or NULL: P2; column j of F~ P2 is column
+ *             perm[j] of F~.
+ *   n2x2      host, or NULL: the number of 2x2 pivots taken.
+ * Allocates its workspace (16 (m + p) n bytes and O(m + p + n)) on the stream
+ * and frees it before returning.  Returns GHSVD_ERR_BREAKDOWN if the
+ * hyperbolic QR breaks down (outputs undefined).
+ */
+ghsvd_status ghsvd_urv(int64_t m, int64_t p, int64_t n, const void *F, int64_t ldf,
+                       const int8_t *J, int64_t n_plus, const void *G, int64_t ldg,
+                       void *Fs, int64_t ldfs, int8_t *Js, void *Gs, int64_t ldgs, int64_t *perm,
+                       int *n2x2, void *stream);
+
+/*
+ * Phase 4 (Section 7): X = Z^{-1} by Gaussian elimination with complete
+ * pivoting, P Z Q = L U, and the solution of Z X = I.
+ *   Z, ldz    device, complex128 n x n, read only.
+ *   X, ldx    device, complex128 n x n (ldx >= n).
+ * n <= 12288.  Allocates its workspace (16 n^2 bytes and O(n^2 / 4096))
+ * on the stream.  Returns GHSVD_ERR_RANK_DEFICIENT if a pivot is exactly
+ * zero (X undefined).
+ */
+ghsvd_status ghsvd_inverse(int64_t n, const void *Z, int64_t ldz, void *X, int64_t ldx, void *stream);
+
+/*
+ * The full GHSVD (eq. 3.1) from the last successful ghsvd_solve on h: with
+ * F', G', Z' the converged columns (Section 6.1.7),
+ *   Sigma_F'_j = |f'_j^* J f'_j|^{1/2}, Sigma_G'_j = ||g'_j||,
+ *   Sigma_j = (Sigma_F'_j^2 + Sigma_G'_j^2)^{1/2},
+ *   Sigma_F = Sigma_F' / Sigma, Sigma_G = Sigma_G' / Sigma (so that
+ *   Sigma_F^2 + Sigma_G^2 = I), Z = Z' Sigma^{-1} and X = Z^{-1} (Phase 4);
+ * U = F' Sigma_F'^{-1} and V = G' Sigma_G'^{-1} are the columns that
+ * ghsvd_get_factors returns, scaled.  Columns follow the iteration's order
+ * (not sorted, whatever sort_ascending says).  After a shortened solve they
+ * refer to the square pencil of ghsvd_urv.
+ *   sigma_f, sigma_g  device, n doubles each, or NULL.
+ *   X, ldx    device, complex128 n x n, or NULL.
+ * Allocates its workspace on the stream.
+ */
+ghsvd_status ghsvd_phase4(ghsvd_t h, double *sigma_f, double *sigma_g, void *X, int64_t ldx,
+                          void *stream);
+
+/*
+ * The relative errors of eq. 7.1 of the GHSVD of the last successful solve
+ * on h: err_f = ||F - U Sigma_F X||_F / ||F||_F and
+ * err_g = ||G - V Sigma_G X||_F / ||G||_F, with U Sigma_F X = F' Sigma^{-1} X
+ * and V Sigma_G X = G' Sigma^{-1} X.
+ *   F, ldf, G, ldg  device: the factors that solve was given (m x n, p x n).
+ *   X, ldx    device: X from ghsvd_phase4.
+ *   err_f, err_g   host.
+ */
+ghsvd_status ghsvd_decomposition_errors(ghsvd_t h, const void *F, int64_t ldf, const void *G,
+                                        int64_t ldg, const void *X, int64_t ldx, double *err_f,
+                                        double *err_g, void *stream);
 
 #ifdef __cplusplus
 }

@@ -77,6 +77,8 @@ struct ghsvd_ctx {
     KTimer timer;
     void *batch = nullptr;              // working memory of ghsvd_solve_batched
     hz::GemmItem *d_item = nullptr;     // one item of the compensated warm-start product
+    void *ozws = nullptr;               // workspace of the split-bf16 update
+    long long cap_ozws = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -116,6 +118,9 @@ static void free_all(ghsvd_ctx *h)
     h->batch = nullptr;
     cudaFree(h->d_item);
     h->d_item = nullptr;
+    cudaFree(h->ozws);
+    h->ozws = nullptr;
+    h->cap_ozws = 0;
     cudaFree(h->W); cudaFree(h->W32); cudaFree(h->Wtmp); cudaFree(h->partial); cudaFree(h->zhat);
     cudaFree(h->pair_flag); cudaFree(h->slotcol); cudaFree(h->Jrow); cudaFree(h->Jdev);
     cudaFree(h->counters); cudaFree(h->err); cudaFree(h->lam_tmp); cudaFree(h->gscale);
@@ -207,6 +212,7 @@ const char *ghsvd_status_string(ghsvd_status s)
     case GHSVD_ERR_NOMEM: return "out of device memory";
     case GHSVD_ERR_SCRATCH_TOO_SMALL:
         return "problem too large for the no-allocation scratch array (GHSVD_NOALLOC_SCRATCH_BYTES)";
+    case GHSVD_ERR_BREAKDOWN: return "hyperbolic QR breakdown (Phase 2)";
     }
     return "unknown status";
 }
@@ -222,7 +228,9 @@ ghsvd_status ghsvd_create(ghsvd_t *out, int device, const ghsvd_opts *opts)
         o.inner_sweeps > 30 || o.max_sweeps < 1 || o.max_sweeps > 1000 ||
         (o.crit_mode != 0 && o.crit_mode != 1) ||
         (o.precision != GHSVD_PRECISION_FP64 && o.precision != GHSVD_PRECISION_MIXED) ||
-        o.mixed_max_sweeps < 0 || o.gram_chunk < 0 || (o.timing != 0 && o.timing != 1))
+        o.mixed_max_sweeps < 0 || o.gram_chunk < 0 || (o.timing != 0 && o.timing != 1) ||
+        (o.shorten != 0 && o.shorten != 1) ||
+        (o.update_engine != GHSVD_UPDATE_FP64 && o.update_engine != GHSVD_UPDATE_SPLIT_BF16))
         return GHSVD_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -306,6 +314,16 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
     long long cap;
     CUDA_TRY(grow(&h->W, Mt * n, &h->cap_w));
     if (mixed) CUDA_TRY(grow(&h->W32, Mt * n, &h->cap_w32));
+    const bool split_update = o.update_engine == GHSVD_UPDATE_SPLIT_BF16 && n >= 2;
+    int oz_R = 1;
+    if (split_update) {
+        // out-of-place updates alternate between W and Wtmp
+        CUDA_TRY(grow(&h->Wtmp, Mt * n, &h->cap_wtmp));
+        char *ozp = (char *)h->ozws;
+        CUDA_TRY(grow(&ozp, (long long)hz::oz_workspace_bytes(n, npairs), &h->cap_ozws));
+        h->ozws = ozp;
+        oz_R = hz::oz_row_groups(Mt, npairs, h->num_sms);
+    }
     const long long npart = (long long)std::max(npairs, 1) * cpp * hz::KKMAX * hz::KKMAX;
     {
         double2 *pp = (double2 *)h->partial;
@@ -451,12 +469,12 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
         while (sweeps < o.max_sweeps) {
             const bool single = phase_single != 0;
             ia.tol = single ? tol32 : tol64;
-            void *Wc = single ? (void *)h->W32 : (void *)h->W;
             CUDA_TRY(cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned long long), st));
             const bool timed = o.timing != 0;
             if (timed) CUDA_TRY(h->timer.reserve(6 * nsteps));
             cudaEvent_t *ev = timed ? h->timer.ev.data() : nullptr;
             for (int r = 0; r < nsteps; ++r) {
+                void *Wc = single ? (void *)h->W32 : (void *)h->W;
                 sa.slotcol = h->slotcol + (size_t)r * npairs * kk;
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 0], st));
                 CUDA_TRY(hz::launch_gram(Wc, single, h->Jrow, sa, h->partial, st));
@@ -466,7 +484,15 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
                                           h->counters, h->err, st));
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 3], st));
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 4], st));
-                CUDA_TRY(hz::launch_update(Wc, single, sa, h->zhat, h->pair_flag, st));
+                if (split_update && !single) {
+                    CUDA_TRY(hz::launch_oz_update(h->W, h->Wtmp, sa, n, h->zhat, h->pair_flag, h->ozws,
+                                                  oz_R, st));
+                    std::swap(h->W, h->Wtmp);
+                    std::swap(h->cap_w, h->cap_wtmp);
+                    h->stats.kernel_launches += 2;     // column exponents, Z^ slices
+                } else {
+                    CUDA_TRY(hz::launch_update(Wc, single, sa, h->zhat, h->pair_flag, st));
+                }
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 5], st));
             }
             h->stats.launches_gram += nsteps;
@@ -561,6 +587,66 @@ static ghsvd_status validate(ghsvd_t h, int64_t m, int64_t p, int64_t n, const v
     return GHSVD_OK;
 }
 
+// Phase 2 then the iteration on the square pencil (opts.shorten), else the
+// iteration on the given factors.  Device pointers, except a host J.
+static ghsvd_status solve_entry(ghsvd_t h, int64_t m, int64_t p, int64_t n, const void *F, int64_t ldf,
+                                const int8_t *J, int64_t n_plus, const void *G, int64_t ldg,
+                                const void *V0, int64_t ldv0, double *lambda, void *V, int64_t ldv,
+                                int *sweeps, cudaStream_t st)
+{
+    if (!h->opts.shorten)
+        return solve_impl(h, m, p, n, F, ldf, J, n_plus, G, ldg, V0, ldv0, lambda, V, ldv, sweeps, st);
+    if (V0) return GHSVD_ERR_INVALID_ARG;
+    auto t0 = std::chrono::steady_clock::now();
+    const size_t wsb = hz::urv_workspace_bytes(m, p, (int)n);
+    void *ws = nullptr, *Fs = nullptr, *Gs = nullptr, *Vs = nullptr;
+    int8_t *Js = nullptr, *Jd = nullptr;
+    int *permi = nullptr, *dflags = nullptr;
+    int hflags[3] = {0, 0, 0};
+    cudaError_t e = cudaMallocAsync(&ws, wsb, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&Fs, 16ull * n * n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&Gs, 16ull * n * n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&Js, (size_t)n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&permi, 4ull * n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dflags, 16, st);
+    if (e == cudaSuccess && V) e = cudaMallocAsync(&Vs, 16ull * n * n, st);
+    if (e == cudaSuccess && J && !is_device_ptr(J)) {
+        e = cudaMallocAsync((void **)&Jd, (size_t)m, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Jd, J, (size_t)m, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess)
+        e = hz::launch_urv((int)m, (int)p, (int)n, (const double2 *)F, ldf, Jd ? Jd : J, n_plus,
+                           (const double2 *)G, ldg, (double2 *)Fs, n, Js, (double2 *)Gs, n, nullptr, permi,
+                           ws, dflags, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, dflags, 12, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const double ms2 =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    ghsvd_status s = status_of(e);
+    if (s == GHSVD_OK && hflags[2]) s = GHSVD_ERR_INVALID_ARG;
+    if (s == GHSVD_OK && hflags[0]) s = GHSVD_ERR_BREAKDOWN;
+    if (s == GHSVD_OK) {
+        s = solve_impl(h, n, n, n, Fs, n, Js, 0, Gs, n, nullptr, 0, lambda, Vs, n, sweeps, st);
+        if (V && (s == GHSVD_OK || s == GHSVD_ERR_NOT_CONVERGED)) {
+            e = hz::launch_permute_rows((const double2 *)Vs, n, (int)n, permi, (double2 *)V, ldv, st);
+            if (e != cudaSuccess) s = status_of(e);
+            h->stats.kernel_launches += 1;
+        }
+        h->stats.kernel_launches += hz::urv_launches((int)n);
+        h->stats.ms_phase2 = ms2;
+        h->stats.n2x2 = hflags[1];
+    }
+    cudaFreeAsync(ws, st); cudaFreeAsync(Fs, st); cudaFreeAsync(Gs, st); cudaFreeAsync(Js, st);
+    cudaFreeAsync(permi, st); cudaFreeAsync(dflags, st);
+    if (Vs) cudaFreeAsync(Vs, st);
+    if (Jd) cudaFreeAsync(Jd, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (s == GHSVD_OK && e2 != cudaSuccess) s = status_of(e2);
+    h->stats.ms_total =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return s;
+}
+
 extern "C" {
 
 ghsvd_status ghsvd_solve_from(ghsvd_t h, int64_t m, int64_t p, int64_t n, const void *F, int64_t ldf,
@@ -577,8 +663,8 @@ ghsvd_status ghsvd_solve_from(ghsvd_t h, int64_t m, int64_t p, int64_t n, const 
     int prev = 0;
     cudaGetDevice(&prev);
     if (cudaSetDevice(h->device) != cudaSuccess) return GHSVD_ERR_CUDA;
-    s = solve_impl(h, m, p, n, F, ldf, J, n_plus, G, ldg, V0, ldv0, lambda, V, ldv, sweeps,
-                   (cudaStream_t)stream);
+    s = solve_entry(h, m, p, n, F, ldf, J, n_plus, G, ldg, V0, ldv0, lambda, V, ldv, sweeps,
+                    (cudaStream_t)stream);
     cudaSetDevice(prev);
     return s;
 }
@@ -618,8 +704,8 @@ ghsvd_status ghsvd_solve_host(ghsvd_t h, int64_t m, int64_t p, int64_t n, const 
                               cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && J) e = cudaMemcpyAsync(dJ, J, (size_t)m, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
-        s = solve_impl(h, m, p, n, dF, m, J ? dJ : nullptr, n_plus, dG, p, nullptr, 0, dl, dV, n,
-                       sweeps, st);
+        s = solve_entry(h, m, p, n, dF, m, J ? dJ : nullptr, n_plus, dG, p, nullptr, 0, dl, dV, n,
+                        sweeps, st);
         if (s == GHSVD_OK || s == GHSVD_ERR_NOT_CONVERGED) {
             e = cudaMemcpyAsync(lambda, dl, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess && V)
@@ -700,3 +786,150 @@ extern "C" ghsvd_status ghsvd_solve_batched(ghsvd_t h, int batch, const int64_t 
     cudaSetDevice(prev);
     return s;
 }
+
+// ---------------------------------------------------------------------------
+// Phase 2 and Phase 4 (Sections 5 and 7)
+// ---------------------------------------------------------------------------
+extern "C" {
+
+ghsvd_status ghsvd_urv(int64_t m, int64_t p, int64_t n, const void *F, int64_t ldf, const int8_t *J,
+                       int64_t n_plus, const void *G, int64_t ldg, void *Fs, int64_t ldfs, int8_t *Js,
+                       void *Gs, int64_t ldgs, int64_t *perm, int *n2x2, void *stream)
+{
+    if (!F || !G || !Fs || !Js || !Gs || n < 1 || m < n || p < n || ldf < m || ldg < p || ldfs < n ||
+        ldgs < n || m > (1LL << 30) || p > (1LL << 30) || n > (1 << 20))
+        return GHSVD_ERR_INVALID_ARG;
+    if (!J && (n_plus < 0 || n_plus > m)) return GHSVD_ERR_INVALID_ARG;
+    if (!is_device_ptr(F) || !is_device_ptr(G) || !is_device_ptr(Fs) || !is_device_ptr(Js) ||
+        !is_device_ptr(Gs) || (perm && !is_device_ptr(perm)) || (J && !is_device_ptr(J)))
+        return GHSVD_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *ws = nullptr;
+    int *dflags = nullptr;
+    int hflags[3] = {0, 0, 0};
+    cudaError_t e = cudaMallocAsync(&ws, hz::urv_workspace_bytes(m, p, (int)n), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dflags, 16, st);
+    if (e == cudaSuccess)
+        e = hz::launch_urv((int)m, (int)p, (int)n, (const double2 *)F, ldf, J, n_plus, (const double2 *)G,
+                           ldg, (double2 *)Fs, ldfs, Js, (double2 *)Gs, ldgs, (long long *)perm, nullptr,
+                           ws, dflags, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, dflags, 12, cudaMemcpyDeviceToHost, st);
+    if (ws) cudaFreeAsync(ws, st);
+    if (dflags) cudaFreeAsync(dflags, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return status_of(e);
+    if (n2x2) *n2x2 = hflags[1];
+    if (hflags[2]) return GHSVD_ERR_INVALID_ARG;
+    return hflags[0] ? GHSVD_ERR_BREAKDOWN : GHSVD_OK;
+}
+
+ghsvd_status ghsvd_inverse(int64_t n, const void *Z, int64_t ldz, void *X, int64_t ldx, void *stream)
+{
+    if (!Z || !X || n < 1 || n > hz::inverse_max_n() || ldz < n || ldx < n) return GHSVD_ERR_INVALID_ARG;
+    if (!is_device_ptr(Z) || !is_device_ptr(X)) return GHSVD_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *ws = nullptr;
+    int *dflag = nullptr;
+    int hflag = 0;
+    cudaError_t e = cudaMallocAsync(&ws, hz::inverse_workspace_bytes((int)n), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dflag, 4, st);
+    if (e == cudaSuccess)
+        e = hz::launch_inverse((int)n, (const double2 *)Z, ldz, (double2 *)X, ldx, ws, dflag, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, dflag, 4, cudaMemcpyDeviceToHost, st);
+    if (ws) cudaFreeAsync(ws, st);
+    if (dflag) cudaFreeAsync(dflag, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return status_of(e);
+    return hflag ? GHSVD_ERR_RANK_DEFICIENT : GHSVD_OK;
+}
+
+ghsvd_status ghsvd_phase4(ghsvd_t h, double *sigma_f, double *sigma_g, void *X, int64_t ldx, void *stream)
+{
+    if (!h || !h->solved) return GHSVD_ERR_INVALID_ARG;
+    const int n = h->n;
+    if (X && (ldx < n || n > hz::inverse_max_n())) return GHSVD_ERR_INVALID_ARG;
+    if ((sigma_f && !is_device_ptr(sigma_f)) || (sigma_g && !is_device_ptr(sigma_g)) ||
+        (X && !is_device_ptr(X)))
+        return GHSVD_ERR_INVALID_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(h->device) != cudaSuccess) return GHSVD_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *sig = nullptr;
+    double2 *Zs = nullptr;
+    void *ws = nullptr;
+    int *dflag = nullptr;
+    int hflag = 0;
+    cudaError_t e = cudaMallocAsync((void **)&sig, 8ull * n, st);
+    if (e == cudaSuccess && X) e = cudaMallocAsync((void **)&Zs, 16ull * n * n, st);
+    if (e == cudaSuccess && X) e = cudaMallocAsync(&ws, hz::inverse_workspace_bytes(n), st);
+    if (e == cudaSuccess && X) e = cudaMallocAsync((void **)&dflag, 4, st);
+    if (e == cudaSuccess)
+        e = hz::launch_sigma(h->W, h->Mt, h->Jrow, h->m_pad, h->p_pad, n, sig, sigma_f, sigma_g, Zs, n, st);
+    if (e == cudaSuccess && X) e = hz::launch_inverse(n, Zs, n, (double2 *)X, ldx, ws, dflag, st);
+    if (e == cudaSuccess && X) e = cudaMemcpyAsync(&hflag, dflag, 4, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(sig, st);
+    if (Zs) cudaFreeAsync(Zs, st);
+    if (ws) cudaFreeAsync(ws, st);
+    if (dflag) cudaFreeAsync(dflag, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaSetDevice(prev);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return status_of(e);
+    return hflag ? GHSVD_ERR_RANK_DEFICIENT : GHSVD_OK;
+}
+
+ghsvd_status ghsvd_decomposition_errors(ghsvd_t h, const void *F, int64_t ldf, const void *G, int64_t ldg,
+                                        const void *X, int64_t ldx, double *err_f, double *err_g,
+                                        void *stream)
+{
+    if (!h || !h->solved || !F || !G || !X || !err_f || !err_g) return GHSVD_ERR_INVALID_ARG;
+    const int n = h->n, m = h->m, p = h->p;
+    if (ldf < m || ldg < p || ldx < n) return GHSVD_ERR_INVALID_ARG;
+    if (!is_device_ptr(F) || !is_device_ptr(G) || !is_device_ptr(X)) return GHSVD_ERR_INVALID_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(h->device) != cudaSuccess) return GHSVD_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long rows = (long long)h->m_pad + h->p_pad;
+    double *sig = nullptr, *part = nullptr, *out = nullptr;
+    double2 *B = nullptr, *C = nullptr;
+    hz::GemmItem *item = nullptr;
+    double hout[2] = {0.0, 0.0};
+    cudaError_t e = cudaMallocAsync((void **)&sig, 8ull * n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&B, 16ull * n * n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&C, 16ull * rows * n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&part, 16ull * 304, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&out, 16, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&item, sizeof(hz::GemmItem), st);
+    // B = Sigma^{-1} X; C = [F'; G'] B = [U Sigma_F X; V Sigma_G X]
+    if (e == cudaSuccess)
+        e = hz::launch_sigma(h->W, h->Mt, h->Jrow, h->m_pad, h->p_pad, n, sig, nullptr, nullptr, nullptr, 0,
+                             st);
+    if (e == cudaSuccess) e = hz::launch_rowscale((const double2 *)X, ldx, n, sig, B, st);
+    const hz::GemmItem it{h->W, h->Mt, rows, B, n, C, rows, n, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(item, &it, sizeof(it), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = hz::launch_gemm_batched(item, 1, rows, n, st);
+    if (e == cudaSuccess)
+        e = hz::launch_rel_err((const double2 *)F, ldf, C, rows, m, n, part, out, st);
+    if (e == cudaSuccess)
+        e = hz::launch_rel_err((const double2 *)G, ldg, C + h->m_pad, rows, p, n, part, out + 1, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hout, out, 16, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(sig, st);
+    if (B) cudaFreeAsync(B, st);
+    if (C) cudaFreeAsync(C, st);
+    if (part) cudaFreeAsync(part, st);
+    if (out) cudaFreeAsync(out, st);
+    if (item) cudaFreeAsync(item, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaSetDevice(prev);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return status_of(e);
+    *err_f = hout[0];
+    *err_g = hout[1];
+    return GHSVD_OK;
+}
+
+}  // extern "C"

@@ -76,7 +76,9 @@ __device__ __forceinline__ void c_left(T2 &x0, T2 &x1, const T *z)
 // TP is the type of the Gram partials, TU the type in which the block
 // pivots are kept and transformed (double for the FP64 sweeps, float for the
 // complex64 preconditioning sweeps).  The 2x2 parameters (eq. 6.5-6.12) are
-// always computed in FP64 from the pivot entries.
+// computed in FP64 from the pivot entries in both: with FP32 parameters the
+// complex64 rounds classify more rotations as small, their big counts no
+// longer level off at the rounding level and the refinement rounds end late.
 //
 // The Gram kernel writes the 16 x 16 tiles on and above the diagonal; a tile
 // below the diagonal is the conjugate transpose of its mirror (the block
@@ -108,8 +110,7 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
         for (int r = 0; r < CL; ++r) copies[r][off] = v;
     };
     const int HS = KKMAX * KKMAX;               // offset of S from H (Z: 2 HS)
-    __shared__ double zp[KKMAX / 2][8];      // the step's 2x2 transformations (FP64)
-    __shared__ TU zu[KKMAX / 2][8];          // the same in the update type
+    __shared__ TU zu[KKMAX / 2][8];          // the step's 2x2 transformations
     __shared__ int tr[KKMAX / 2];            // pivot transformed?
     __shared__ int pslot[KKMAX];             // slots of pivot l: 2l, 2l+1
     __shared__ int valid[KKMAX];
@@ -163,13 +164,18 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                     pslot[2 * l] = pa;
                     pslot[2 * l + 1] = pb;
                     int rc = PIV_NONE, big = 0;
+                    double zl[8];
                     if (valid[pa] && valid[pb]) {
                         const U2 hab = H[pa + kk * pb], sab = S[pa + kk * pb];
-                        rc = pivot2x2((double)H[pa + kk * pa].x, (double)H[pb + kk * pb].x,
-                                      (double)hab.x, (double)hab.y, (double)S[pa + kk * pa].x,
-                                      (double)S[pb + kk * pb].x, (double)sab.x, (double)sab.y,
-                                      a.tol, a.crit_mode, zp[l], &big);
+                        rc = pivot2x2<double>((double)H[pa + kk * pa].x, (double)H[pb + kk * pb].x,
+                                              (double)hab.x, (double)hab.y, (double)S[pa + kk * pa].x,
+                                              (double)S[pb + kk * pb].x, (double)sab.x, (double)sab.y,
+                                              a.tol, a.crit_mode, zl, &big);
                     }
+                    // complex64 preconditioning sweeps leave a pivot that looks
+                    // dependent at their rounding level alone; the FP64 sweeps
+                    // that follow decide about rank deficiency
+                    if (rc == PIV_ERR_RANK && sizeof(TU) == sizeof(float)) rc = PIV_NONE;
                     if (rc < 0) {
                         atomicOr(&s_err, rc == PIV_ERR_RANK ? DEVERR_RANK : DEVERR_NONFINITE);
                         rc = PIV_NONE;
@@ -177,7 +183,7 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                     tr[l] = rc == PIV_TRANSFORM;
                     if (rc == PIV_TRANSFORM) {
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) zu[l][q] = (TU)zp[l][q];
+                        for (int q = 0; q < 8; ++q) zu[l][q] = (TU)zl[q];
                         my_all += 1;
                         my_big += big;
                         step_all += 1;

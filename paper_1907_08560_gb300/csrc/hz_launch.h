@@ -89,6 +89,36 @@ cudaError_t launch_eye32(void *W, long long ld, int r0, int n, int n_pad, cudaSt
 cudaError_t launch_extract(const double2 *W, long long ld, int r0, int rows, int n, double2 *out,
                            long long ldo, cudaStream_t s);
 
+// The block update on the bf16 tensor cores with FP64 accuracy (hz_ozaki.cu).
+size_t oz_workspace_bytes(int n, int npairs);
+cudaError_t setup_ozaki();
+int oz_row_groups(long long Mt, int npairs, int sms);
+cudaError_t launch_oz_update(const double2 *W, double2 *Wout, const StepArgs &a, int n, const double2 *zhat,
+                             const int *pair_flag, void *ws, int R, cudaStream_t s);
+
+// Phase 2 (hz_urv.cu): the (J, I) URV shortening of Section 5.
+size_t urv_workspace_bytes(long long m, long long p, int n);
+cudaError_t launch_urv(int m, int p, int n, const double2 *F, long long ldf, const int8_t *J,
+                       long long n_plus, const double2 *G, long long ldg, double2 *Fs, long long ldfs,
+                       int8_t *Js, double2 *Gs, long long ldgs, long long *perm_out, int *permi,
+                       void *ws, int *d_flags, cudaStream_t s);
+int urv_launches(int n);
+
+// Phase 4 (hz_phase4.cu): X = Z^{-1} and the pieces of eq. 7.1.
+size_t inverse_workspace_bytes(int n);
+int inverse_max_n();
+cudaError_t launch_inverse(int n, const double2 *Z, long long ldz, double2 *X, long long ldx, void *ws,
+                           int *d_flag, cudaStream_t s);
+int inverse_launches(int n);
+cudaError_t launch_sigma(const double2 *W, long long ld, const int8_t *Jrow, int m_pad, int p_pad, int n,
+                         double *sig, double *sf, double *sg, double2 *Zs, long long ldz, cudaStream_t s);
+cudaError_t launch_rowscale(const double2 *X, long long ldx, int n, const double *sig, double2 *B,
+                            cudaStream_t s);
+cudaError_t launch_rel_err(const double2 *A, long long lda, const double2 *C, long long ldc, int rows, int n,
+                           double *part, double *out, cudaStream_t s);
+cudaError_t launch_permute_rows(const double2 *src, long long lds, int n, const int *perm, double2 *dst,
+                                long long ldd, cudaStream_t s);
+
 }  // namespace hz
 
 // Batched solves (hz_batch.cu).

@@ -25,9 +25,12 @@ GHSVD_ERR_NOT_CONVERGED = 4
 GHSVD_ERR_CUDA = 5
 GHSVD_ERR_NOMEM = 6
 GHSVD_ERR_SCRATCH_TOO_SMALL = 7
+GHSVD_ERR_BREAKDOWN = 8
 
 GHSVD_PRECISION_FP64 = 0
 GHSVD_PRECISION_MIXED = 1
+GHSVD_UPDATE_FP64 = 0
+GHSVD_UPDATE_SPLIT_BF16 = 1
 
 
 class ghsvd_opts(ctypes.Structure):
@@ -35,7 +38,8 @@ class ghsvd_opts(ctypes.Structure):
                 ("max_sweeps", ctypes.c_int), ("crit_mode", ctypes.c_int),
                 ("precision", ctypes.c_int), ("mixed_max_sweeps", ctypes.c_int),
                 ("sort_ascending", ctypes.c_int), ("gram_chunk", ctypes.c_int),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("shorten", ctypes.c_int),
+                ("update_engine", ctypes.c_int)]
 
 
 class ghsvd_stats(ctypes.Structure):
@@ -47,7 +51,8 @@ class ghsvd_stats(ctypes.Structure):
                 ("launches_gram", ctypes.c_longlong), ("launches_inner", ctypes.c_longlong),
                 ("launches_update", ctypes.c_longlong), ("ms_gram", ctypes.c_double),
                 ("ms_inner", ctypes.c_double), ("ms_update", ctypes.c_double),
-                ("rounds_low", ctypes.c_int)]
+                ("rounds_low", ctypes.c_int), ("ms_phase2", ctypes.c_double),
+                ("n2x2", ctypes.c_int)]
 
 
 class GhsvdError(RuntimeError):
@@ -123,6 +128,17 @@ def load(path: str | None = None):
     lib.ghsvd_align_phases.argtypes = [i64, vp, i64, vp, i64, vp]
     lib.ghsvd_status_string.restype = ctypes.c_char_p
     lib.ghsvd_status_string.argtypes = [c_int]
+    lib.ghsvd_urv.restype = c_int
+    lib.ghsvd_urv.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, vp, i64, vp,
+                              ctypes.POINTER(c_int), vp]
+    lib.ghsvd_inverse.restype = c_int
+    lib.ghsvd_inverse.argtypes = [i64, vp, i64, vp, i64, vp]
+    lib.ghsvd_phase4.restype = c_int
+    lib.ghsvd_phase4.argtypes = [vp, vp, vp, vp, i64, vp]
+    lib.ghsvd_decomposition_errors.restype = c_int
+    lib.ghsvd_decomposition_errors.argtypes = [vp, vp, i64, vp, i64, vp, i64,
+                                               ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double), vp]
     if path is None:
         _lib = lib
     return lib
@@ -482,7 +498,64 @@ def ghsvd_get_stats(h) -> dict:
                 kernel_launches=st.kernel_launches, launches_gram=st.launches_gram,
                 launches_inner=st.launches_inner, launches_update=st.launches_update,
                 ms_gram=st.ms_gram, ms_inner=st.ms_inner, ms_update=st.ms_update,
-                rounds_low=st.rounds_low)
+                rounds_low=st.rounds_low, ms_phase2=st.ms_phase2, n2x2=st.n2x2)
+
+
+def ghsvd_urv(F, J, G, n_plus: int | None = None, stream=None):
+    """Phase 2 (Section 5): the square (Fs, Js, Gs) of a tall (F, J, G) on the device.
+
+    Returns (Fs, Js, Gs, perm, n2x2): Fs, Gs n x n column-major complex128,
+    Js int8 (n), perm int64 (n) with F[:, perm] = F P2."""
+    import torch
+    m, n = F.shape
+    p = G.shape[0]
+    if n_plus is None:
+        n_plus = m
+    dev = F.device
+    Fs = torch.empty_strided((n, n), (1, n), dtype=torch.complex128, device=dev)
+    Gs = torch.empty_strided((n, n), (1, n), dtype=torch.complex128, device=dev)
+    Js = torch.empty(n, dtype=torch.int8, device=dev)
+    perm = torch.empty(n, dtype=torch.int64, device=dev)
+    Jp = None
+    if J is not None:
+        if J.dtype != torch.int8 or not J.is_cuda:
+            raise TypeError("J must be an int8 CUDA tensor")
+        J = J.contiguous()
+        Jp = ctypes.c_void_p(J.data_ptr())
+    n2 = ctypes.c_int(0)
+    _check(load().ghsvd_urv(m, p, n, F.data_ptr(), ld_of(F), Jp, n_plus, G.data_ptr(), ld_of(G),
+                            Fs.data_ptr(), n, Js.data_ptr(), Gs.data_ptr(), n, perm.data_ptr(),
+                            ctypes.byref(n2), _stream_ptr(stream)))
+    return Fs, Js, Gs, perm, n2.value
+
+
+def ghsvd_inverse(Z, stream=None):
+    """Phase 4 (Section 7): X = Z^{-1} by complete pivoting, on the device."""
+    import torch
+    n = Z.shape[0]
+    X = torch.empty_strided((n, n), (1, n), dtype=torch.complex128, device=Z.device)
+    _check(load().ghsvd_inverse(n, Z.data_ptr(), ld_of(Z), X.data_ptr(), n, _stream_ptr(stream)))
+    return X
+
+
+def ghsvd_phase4(h, n: int, device="cuda", stream=None):
+    """(Sigma_F, Sigma_G, X) of the full GHSVD of the last solve on h (eq. 3.1)."""
+    import torch
+    sf = torch.empty(n, dtype=torch.float64, device=device)
+    sg = torch.empty(n, dtype=torch.float64, device=device)
+    X = torch.empty_strided((n, n), (1, n), dtype=torch.complex128, device=device)
+    _check(load().ghsvd_phase4(h, sf.data_ptr(), sg.data_ptr(), X.data_ptr(), n, _stream_ptr(stream)))
+    return sf, sg, X
+
+
+def ghsvd_decomposition_errors(h, F, G, X, stream=None):
+    """The relative errors of eq. 7.1 for the last solve on h: (err_F, err_G)."""
+    ef = ctypes.c_double(0.0)
+    eg = ctypes.c_double(0.0)
+    _check(load().ghsvd_decomposition_errors(h, F.data_ptr(), ld_of(F), G.data_ptr(), ld_of(G),
+                                             X.data_ptr(), ld_of(X), ctypes.byref(ef),
+                                             ctypes.byref(eg), _stream_ptr(stream)))
+    return ef.value, eg.value
 
 
 class Solver:
@@ -503,6 +576,12 @@ class Solver:
 
     def factors(self, m, p, n, **kw):
         return ghsvd_get_factors(self.h, m, p, n, **kw)
+
+    def phase4(self, n, **kw):
+        return ghsvd_phase4(self.h, n, **kw)
+
+    def decomposition_errors(self, F, G, X, **kw):
+        return ghsvd_decomposition_errors(self.h, F, G, X, **kw)
 
     def stats(self):
         return ghsvd_get_stats(self.h)

@@ -39,15 +39,15 @@ def test_default_opts_and_status_strings(lib):
     from paper_1907_08560_gb300 import ghsvd
     o = ghsvd.ghsvd_default_opts()
     assert (o.block_width, o.inner_sweeps, o.max_sweeps, o.crit_mode, o.precision) == (32, 1, 30, 0, 0)
-    for s in range(7):
-        assert ghsvd.status_string(s)
+    for s in range(9):
+        assert ghsvd.status_string(s) != "unknown status"
     assert ghsvd.status_string(99) == "unknown status"
 
 
 def test_create_rejects_bad_options(lib):
     from paper_1907_08560_gb300 import ghsvd
     for bad in (dict(block_width=0), dict(block_width=33), dict(inner_sweeps=0),
-                dict(max_sweeps=0), dict(crit_mode=2), dict(precision=5)):
+                dict(max_sweeps=0), dict(crit_mode=2), dict(precision=5), dict(shorten=2)):
         o = ghsvd.ghsvd_default_opts(**bad)
         h = ctypes.c_void_p()
         s = lib.ghsvd_create(ctypes.byref(h), 0, ctypes.byref(o))
@@ -61,6 +61,13 @@ def test_null_arguments_are_rejected(lib):
     assert lib.ghsvd_get_stats(None, None) == ghsvd.GHSVD_ERR_INVALID_ARG
     lib.ghsvd_destroy(None)
     s = lib.ghsvd_solve(None, 4, 4, 4, None, 4, None, 0, None, 4, None, None, 4, None, None)
+    assert s == ghsvd.GHSVD_ERR_INVALID_ARG
+    s = lib.ghsvd_urv(6, 6, 4, None, 6, None, 3, None, 6, None, 4, None, None, 4, None, None, None)
+    assert s == ghsvd.GHSVD_ERR_INVALID_ARG
+    assert lib.ghsvd_inverse(4, None, 4, None, 4, None) == ghsvd.GHSVD_ERR_INVALID_ARG
+    assert lib.ghsvd_inverse(0, None, 4, None, 4, None) == ghsvd.GHSVD_ERR_INVALID_ARG
+    assert lib.ghsvd_phase4(None, None, None, None, 4, None) == ghsvd.GHSVD_ERR_INVALID_ARG
+    s = lib.ghsvd_decomposition_errors(None, None, 4, None, 4, None, 4, None, None, None)
     assert s == ghsvd.GHSVD_ERR_INVALID_ARG
 
 
