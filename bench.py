@@ -393,8 +393,6 @@ def main():
     ap.add_argument("--mixed-steps", type=int, default=1,
                     help="timed solves of the mixed-precision schedule (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--split-steps", type=int, default=1,
-                    help="timed solves with the block update on the bf16 tensor cores (0: skip)")
     ap.add_argument("--phase2-steps", type=int, default=1,
                     help="timed solves with Phase 2 shortening first (0: skip)")
     ap.add_argument("--no-phase4", dest="phase4", action="store_false",
@@ -539,8 +537,7 @@ def main():
     # converged columns and the per-eigenvalue tolerance (cond by construction:
     # F 1e6, G 10^5; the hyperbolic amplification a_j of the converged columns)
     ref64 = None
-    if args.precision == "fp64" and (args.mixed_steps > 0 or args.phase2_steps > 0 or args.phase4 or
-                                     args.split_steps > 0):
+    if args.precision == "fp64" and (args.mixed_steps > 0 or args.phase2_steps > 0 or args.phase4):
         lam64, _, _, _ = solver.solve(Fd, Gd, Jd, stream=stream)
         Fp64, _, _ = solver.factors(M, P, N)
         lam64 = lam64.cpu().numpy()
@@ -631,45 +628,6 @@ def main():
                      "eig_rel_diff_over_tol_max": eratio}
         ssolver.close()
 
-    # the FP64 solve with the block update on the bf16 tensor cores (FP64
-    # accuracy by exact integer slices); same pencil, same stopping rule
-    split = None
-    if ref64 is not None and args.split_steps > 0:
-        psolver = ghsvd.Solver(local, block_width=W_BLOCK, max_sweeps=args.max_sweeps, timing=1,
-                               update_engine=ghsvd.GHSVD_UPDATE_SPLIT_BF16)
-        psolver.solve(Fd, Gd, Jd, stream=stream)          # warm-up
-        torch.cuda.synchronize()
-        barrier()
-        p0 = torch.cuda.Event(enable_timing=True)
-        p1 = torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        pst, pupd, pl = [], 0.0, 0
-        for _ in range(args.split_steps):
-            lam_p, _, sw_p, st_p = psolver.solve(Fd, Gd, Jd, stream=stream)
-            pst.append(st_p)
-            ps = psolver.stats()
-            pupd += ps["ms_update"]
-            pl += ps["launches_update"]
-        p1.record(stream)
-        torch.cuda.synchronize()
-        sp_ms = allreduce(p0.elapsed_time(p1), dist.ReduceOp.MAX if dist else None)
-        emax, eratio = eig_vs_fp64(lam_p)
-        pvalue = world * args.split_steps / (sp_ms / 1e3)
-        upd_launch_ms = pupd / max(pl, 1)
-        mma_flops = 36 * update_flops_per_launch()      # slice products actually issued (K = 128)
-        bf16_peak = measured_bf16_peak()
-        split = {"value": pvalue, "unit": "solves/s", "ms_per_step": sp_ms / args.split_steps,
-                 "speedup_vs_fp64_update": pvalue / value, "status": pst,
-                 "sweeps": psolver.stats()["sweeps"],
-                 "update_ms_per_launch": upd_launch_ms,
-                 "update_fp64_equivalent_tflops": update_flops_per_launch() / (upd_launch_ms * 1e-3) / 1e12,
-                 "update_bf16_tflops": mma_flops / (upd_launch_ms * 1e-3) / 1e12,
-                 "bf16_peak_measured": bf16_peak,
-                 "update_bf16_frac_of_measured_peak":
-                     (mma_flops / (upd_launch_ms * 1e-3) / 1e12) / bf16_peak if bf16_peak else None,
-                 "eig_rel_diff_vs_fp64_max": emax, "eig_rel_diff_over_tol_max": eratio}
-        psolver.close()
-
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(F, G, J, round(sweeps_per_solve))
@@ -686,7 +644,7 @@ def main():
                            "status": status, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (235 MB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed_precision": mixed,
-                "phase2_shortened": shortened, "phase4": phase4, "split_bf16_update": split,
+                "phase2_shortened": shortened, "phase4": phase4,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -701,15 +659,6 @@ def solver_host(ghsvd, solver, Fpin, Gpin, Jpin, lam_pin, V_pin):
                              Gpin.data_ptr(), P, lam_pin.data_ptr(), V_pin.data_ptr(), N,
                              ctypes.byref(sweeps), None)
     return s
-
-
-def measured_bf16_peak():
-    """Dense bf16 TFLOP/s measured on this machine's GPUs (burst), if recorded."""
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["bf16_tflops"])
-    except (OSError, KeyError, ValueError):
-        return None
 
 
 def measure_fp64_peak(device):

@@ -62,14 +62,6 @@ typedef enum {
                                       finishing sweeps; the 2x2 parameters,
                                       J-norms and the stopping test are FP64  */
 
-/* Engines of the FP64 block update (Section 6.4.3). */
-#define GHSVD_UPDATE_FP64 0        /* FP64 FMA on the CUDA cores                   */
-#define GHSVD_UPDATE_SPLIT_BF16 1  /* the same product with FP64 accuracy on the bf16
-                                      tensor cores: the FP64 operands are cut into
-                                      8 exact 7-bit integer slices, the slice
-                                      products accumulate exactly in FP32 and are
-                                      combined exactly in 64-bit integers         */
-
 typedef struct {
     int block_width;     /* w: maximal block-column width, 1..32 (Section 6.4.1);
                             default 32; 0: automatic (32 for one pencil, the
@@ -95,9 +87,6 @@ typedef struct {
                             Not with a warm start.  0 (default): the tall
                             factors.  ghsvd_solve_batched and
                             ghsvd_solve_noalloc ignore it.                    */
-    int update_engine;   /* GHSVD_UPDATE_FP64 (default) or GHSVD_UPDATE_SPLIT_BF16
-                            for the FP64 sweeps of ghsvd_solve; the batched and
-                            the no-allocation solves use GHSVD_UPDATE_FP64    */
 } ghsvd_opts;
 
 /* Per-solve statistics (Section 6.4.3, "Completing a sweep"). */

@@ -77,8 +77,6 @@ struct ghsvd_ctx {
     KTimer timer;
     void *batch = nullptr;              // working memory of ghsvd_solve_batched
     hz::GemmItem *d_item = nullptr;     // one item of the compensated warm-start product
-    void *ozws = nullptr;               // workspace of the split-bf16 update
-    long long cap_ozws = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -118,9 +116,6 @@ static void free_all(ghsvd_ctx *h)
     h->batch = nullptr;
     cudaFree(h->d_item);
     h->d_item = nullptr;
-    cudaFree(h->ozws);
-    h->ozws = nullptr;
-    h->cap_ozws = 0;
     cudaFree(h->W); cudaFree(h->W32); cudaFree(h->Wtmp); cudaFree(h->partial); cudaFree(h->zhat);
     cudaFree(h->pair_flag); cudaFree(h->slotcol); cudaFree(h->Jrow); cudaFree(h->Jdev);
     cudaFree(h->counters); cudaFree(h->err); cudaFree(h->lam_tmp); cudaFree(h->gscale);
@@ -229,8 +224,7 @@ ghsvd_status ghsvd_create(ghsvd_t *out, int device, const ghsvd_opts *opts)
         (o.crit_mode != 0 && o.crit_mode != 1) ||
         (o.precision != GHSVD_PRECISION_FP64 && o.precision != GHSVD_PRECISION_MIXED) ||
         o.mixed_max_sweeps < 0 || o.gram_chunk < 0 || (o.timing != 0 && o.timing != 1) ||
-        (o.shorten != 0 && o.shorten != 1) ||
-        (o.update_engine != GHSVD_UPDATE_FP64 && o.update_engine != GHSVD_UPDATE_SPLIT_BF16))
+        (o.shorten != 0 && o.shorten != 1))
         return GHSVD_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -314,16 +308,6 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
     long long cap;
     CUDA_TRY(grow(&h->W, Mt * n, &h->cap_w));
     if (mixed) CUDA_TRY(grow(&h->W32, Mt * n, &h->cap_w32));
-    const bool split_update = o.update_engine == GHSVD_UPDATE_SPLIT_BF16 && n >= 2;
-    int oz_R = 1;
-    if (split_update) {
-        // out-of-place updates alternate between W and Wtmp
-        CUDA_TRY(grow(&h->Wtmp, Mt * n, &h->cap_wtmp));
-        char *ozp = (char *)h->ozws;
-        CUDA_TRY(grow(&ozp, (long long)hz::oz_workspace_bytes(n, npairs), &h->cap_ozws));
-        h->ozws = ozp;
-        oz_R = hz::oz_row_groups(Mt, npairs, h->num_sms);
-    }
     const long long npart = (long long)std::max(npairs, 1) * cpp * hz::KKMAX * hz::KKMAX;
     {
         double2 *pp = (double2 *)h->partial;
@@ -484,15 +468,7 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
                                           h->counters, h->err, st));
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 3], st));
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 4], st));
-                if (split_update && !single) {
-                    CUDA_TRY(hz::launch_oz_update(h->W, h->Wtmp, sa, n, h->zhat, h->pair_flag, h->ozws,
-                                                  oz_R, st));
-                    std::swap(h->W, h->Wtmp);
-                    std::swap(h->cap_w, h->cap_wtmp);
-                    h->stats.kernel_launches += 2;     // column exponents, Z^ slices
-                } else {
-                    CUDA_TRY(hz::launch_update(Wc, single, sa, h->zhat, h->pair_flag, st));
-                }
+                CUDA_TRY(hz::launch_update(Wc, single, sa, h->zhat, h->pair_flag, st));
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 5], st));
             }
             h->stats.launches_gram += nsteps;

@@ -89,13 +89,6 @@ cudaError_t launch_eye32(void *W, long long ld, int r0, int n, int n_pad, cudaSt
 cudaError_t launch_extract(const double2 *W, long long ld, int r0, int rows, int n, double2 *out,
                            long long ldo, cudaStream_t s);
 
-// The block update on the bf16 tensor cores with FP64 accuracy (hz_ozaki.cu).
-size_t oz_workspace_bytes(int n, int npairs);
-cudaError_t setup_ozaki();
-int oz_row_groups(long long Mt, int npairs, int sms);
-cudaError_t launch_oz_update(const double2 *W, double2 *Wout, const StepArgs &a, int n, const double2 *zhat,
-                             const int *pair_flag, void *ws, int R, cudaStream_t s);
-
 // Phase 2 (hz_urv.cu): the (J, I) URV shortening of Section 5.
 size_t urv_workspace_bytes(long long m, long long p, int n);
 cudaError_t launch_urv(int m, int p, int n, const double2 *F, long long ldf, const int8_t *J,

@@ -536,8 +536,6 @@ cudaError_t setup_kernels()
     e = cudaFuncSetAttribute(update_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(2 * sizeof(float2) * KKMAX * KKMAX));
     if (e != cudaSuccess) return e;
-    e = setup_ozaki();
-    if (e != cudaSuccess) return e;
     if (g_cluster_mask < 0) {
         int m64 = 0, m32 = 0;
         const char *env = getenv("GHSVD_INNER_CLUSTER");

@@ -29,8 +29,6 @@ GHSVD_ERR_BREAKDOWN = 8
 
 GHSVD_PRECISION_FP64 = 0
 GHSVD_PRECISION_MIXED = 1
-GHSVD_UPDATE_FP64 = 0
-GHSVD_UPDATE_SPLIT_BF16 = 1
 
 
 class ghsvd_opts(ctypes.Structure):
@@ -38,8 +36,7 @@ class ghsvd_opts(ctypes.Structure):
                 ("max_sweeps", ctypes.c_int), ("crit_mode", ctypes.c_int),
                 ("precision", ctypes.c_int), ("mixed_max_sweeps", ctypes.c_int),
                 ("sort_ascending", ctypes.c_int), ("gram_chunk", ctypes.c_int),
-                ("timing", ctypes.c_int), ("shorten", ctypes.c_int),
-                ("update_engine", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("shorten", ctypes.c_int)]
 
 
 class ghsvd_stats(ctypes.Structure):
