@@ -10,10 +10,11 @@ namespace hz {
 // One CTA per (pair, row chunk); the CTA writes the partial Gram of its rows;
 // the inner kernel sums the partials in a fixed order.
 //
-// The block pivots are Hermitian, so only the 16 x 16 tiles on and above the
-// diagonal are computed (10 of 16 for kk = 64, 3 of 4 for kk = 32): 16 threads
-// per tile, each a 4 x 4 set of complex outputs (rows 16 ti + ly + 4i,
-// columns 16 tj + lx + 4j).  J enters as a sign flip of the conjugated factor
+// The block pivots are Hermitian, so only the entries on and above the
+// diagonal are computed: the 16 x 16 tiles on and above the diagonal (10 of 16
+// for kk = 64, 3 of 4 for kk = 32), 16 threads per tile, each a 4 x 4 set of
+// complex outputs (rows 16 ti + ly + 4i, columns 16 tj + lx + 4j); in the
+// diagonal tiles the 4 x 4 blocks below the diagonal are skipped.  J enters as a sign flip of the conjugated factor
 // (an integer xor on the sign bits).
 // ---------------------------------------------------------------------------
 // The body, for one (pair, row chunk): rows [r0, r1) of W (ld), the pair's
@@ -30,14 +31,23 @@ __device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict_
     __shared__ U sgn[GRAM_KT];
     __shared__ int cols[KKMAX];
     const int tid = threadIdx.x, nthr = blockDim.x;
-    // upper-triangular tile (ti, tj) of this thread, row-major order
+    // tile (ti, tj) of this thread: the nt diagonal tiles first (so that
+    // warps hold two diagonal tiles or two off-diagonal ones), then the
+    // tiles above the diagonal in row-major order
     const int nt = (kk + 15) >> 4;
     const int ntiles = nt * (nt + 1) / 2;
     const int tile = tid >> 4, lx = tid & 3, ly = (tid >> 2) & 3;
     const bool active = tile < ntiles;
-    int ti = 0, rem = active ? tile : 0;
-    while (rem >= nt - ti) { rem -= nt - ti; ++ti; }
-    const int qr = 16 * ti, qc = 16 * (ti + rem);
+    int ti = 0, tj = 0;
+    if (active && tile < nt) {
+        ti = tj = tile;
+    } else if (active) {
+        int rem = tile - nt;
+        while (rem >= nt - 1 - ti) { rem -= nt - 1 - ti; ++ti; }
+        tj = ti + 1 + rem;
+    }
+    const bool diag = ti == tj;
+    const int qr = 16 * ti, qc = 16 * tj;
     for (int s = tid; s < KKMAX; s += nthr) cols[s] = s < kk ? slot[s] : -1;
     const U signbit = (U)1 << (sizeof(T) * 8 - 1);
 
@@ -78,25 +88,39 @@ __device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict_
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) y[j] = xs[k][qc + lx + 4 * j];
-            // acc_ij += conj(J x_i) y_j
+            // acc_ij += conj(J x_i) y_j; in a diagonal tile the entries below
+            // the diagonal (i > j) are not needed (the block pivot is Hermitian)
+            if (diag) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    accr[i][j] = fma(x[i].x, y[j].x, accr[i][j]);
-                    accr[i][j] = fma(x[i].y, y[j].y, accr[i][j]);
-                    acci[i][j] = fma(x[i].x, y[j].y, acci[i][j]);
-                    acci[i][j] = fma(-x[i].y, y[j].x, acci[i][j]);
-                }
+                    for (int j = i; j < 4; ++j) {
+                        accr[i][j] = fma(x[i].x, y[j].x, accr[i][j]);
+                        accr[i][j] = fma(x[i].y, y[j].y, accr[i][j]);
+                        acci[i][j] = fma(x[i].x, y[j].y, acci[i][j]);
+                        acci[i][j] = fma(-x[i].y, y[j].x, acci[i][j]);
+                    }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        accr[i][j] = fma(x[i].x, y[j].x, accr[i][j]);
+                        accr[i][j] = fma(x[i].y, y[j].y, accr[i][j]);
+                        acci[i][j] = fma(x[i].x, y[j].y, acci[i][j]);
+                        acci[i][j] = fma(-x[i].y, y[j].x, acci[i][j]);
+                    }
+            }
         }
     }
-    // out[i + KKMAX j] (column-major), computed tiles only
+    // out[i + KKMAX j] (column-major), entries on and above the diagonal only
     if (!active) return;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int ii = qr + ly + 4 * i, jj = qc + lx + 4 * j;
+            if (ii > jj) continue;
             T2 v;
             v.x = accr[i][j];
             v.y = acci[i][j];
@@ -106,7 +130,7 @@ __device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict_
 
 // One outer step of one pencil: CTA = (pair, row chunk).
 template <typename T>
-__global__ void __launch_bounds__(160)
+__global__ void __launch_bounds__(160, 3)
 gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict__ Jrow,
             StepArgs a, typename cplx<T>::t *__restrict__ partial)
 {

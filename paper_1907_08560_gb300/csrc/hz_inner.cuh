@@ -74,15 +74,14 @@ __device__ __forceinline__ void c_left(T2 &x0, T2 &x1, const T *z)
 // computed, the mirror block is its conjugate transpose.
 //
 // TP is the type of the Gram partials, TU the type in which the block
-// pivots are kept and transformed (double for the FP64 sweeps, float for the
-// complex64 preconditioning sweeps).  The 2x2 parameters (eq. 6.5-6.12) are
-// computed in FP64 from the pivot entries in both: with FP32 parameters the
-// complex64 rounds classify more rotations as small, their big counts no
-// longer level off at the rounding level and the refinement rounds end late.
+// pivots are kept and transformed and the 2x2 parameters (eq. 6.5-6.12) are
+// computed: double for the FP64 sweeps, float for the complex64
+// preconditioning sweeps.  The complex64 sweeps still count "big" as FP64
+// would (sin(phi) or sin(psi) >= 2^-27), which keeps the stagnation test of
+// the mixed schedule's refinement rounds as with FP64 parameters.
 //
-// The Gram kernel writes the 16 x 16 tiles on and above the diagonal; a tile
-// below the diagonal is the conjugate transpose of its mirror (the block
-// pivots are Hermitian).
+// The Gram kernel writes the entries on and above the diagonal; an entry
+// below it is the conjugate of its mirror (the block pivots are Hermitian).
 // One CTA (1024 threads) per block pivot; H^, S^, Z^ live in shared memory.
 // ---------------------------------------------------------------------------
 // The body, for one block pivot: pp = its cpp Gram partials, slot = its kk
@@ -127,7 +126,7 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
     // CTA of a cluster sums 1/CL of the entries and stores them in all copies
     for (int idx = tid * CL + crank; idx < kk * kk; idx += CL * blockDim.x) {
         const int i = idx % kk, j = idx / kk;
-        const bool mirror = (i >> 4) > (j >> 4);    // a tile below the diagonal
+        const bool mirror = i > j;                  // below the diagonal: conj of (j, i)
         const int e = mirror ? j + KKMAX * i : i + KKMAX * j;
         double hr = 0, hi = 0, sr = 0, si = 0;
         for (int c = 0; c < a.chunks_h; ++c) {
@@ -164,13 +163,12 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                     pslot[2 * l] = pa;
                     pslot[2 * l + 1] = pb;
                     int rc = PIV_NONE, big = 0;
-                    double zl[8];
+                    TU zl[8];
                     if (valid[pa] && valid[pb]) {
                         const U2 hab = H[pa + kk * pb], sab = S[pa + kk * pb];
-                        rc = pivot2x2<double>((double)H[pa + kk * pa].x, (double)H[pb + kk * pb].x,
-                                              (double)hab.x, (double)hab.y, (double)S[pa + kk * pa].x,
-                                              (double)S[pb + kk * pb].x, (double)sab.x, (double)sab.y,
-                                              a.tol, a.crit_mode, zl, &big);
+                        rc = pivot2x2<TU>(H[pa + kk * pa].x, H[pb + kk * pb].x, hab.x, hab.y,
+                                          S[pa + kk * pa].x, S[pb + kk * pb].x, sab.x, sab.y,
+                                          (TU)a.tol, a.crit_mode, zl, &big);
                     }
                     // complex64 preconditioning sweeps leave a pivot that looks
                     // dependent at their rounding level alone; the FP64 sweeps
@@ -183,7 +181,7 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                     tr[l] = rc == PIV_TRANSFORM;
                     if (rc == PIV_TRANSFORM) {
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) zu[l][q] = (TU)zl[q];
+                        for (int q = 0; q < 8; ++q) zu[l][q] = zl[q];
                         my_all += 1;
                         my_big += big;
                         step_all += 1;

@@ -4,8 +4,8 @@
 //   H^ = [hpp hpq; conj(hpq) hqq],  S^ = [spp spq; conj(spq) sqq],
 // decide by eq. 6.12 whether to transform and build Z' = D0^ Z^ from
 // eq. 6.5, 6.7, 6.10 and 6.11, with the exceptional cases of Section 6.1.6.
-// The parameters are computed in FP64, whatever the precision of the data
-// they are applied to (the template also admits FP32).
+// The FP64 sweeps compute the parameters in FP64; the complex64 sweeps of
+// the mixed schedule in FP32, with the big/small classification of FP64.
 //
 // Readings where the paper is silent or garbled:
 //   - eq. 6.12 is applied to the prescaled pivot with square roots of the
@@ -55,7 +55,9 @@ constexpr int PIV_ERR_RANK = -2;
 constexpr int PIV_ERR_NONFINITE = -3;
 
 // z[0..7] = re/im of z11, z12, z21, z22 (row-major 2x2) on PIV_TRANSFORM.
-// T = double in the library; T = float gives the same steps in FP32.
+// T = double for the FP64 sweeps; T = float for the complex64 sweeps (their
+// data are complex64), where "big" is decided by the FP64 criterion on
+// sin(phi) and sin(psi) rather than by cos = 1 in FP32.
 template <typename T>
 __device__ __forceinline__ int pivot2x2(T hpp, T hqq, T hpq_re, T hpq_im, T spp, T sqq, T spq_re,
                                         T spq_im, T tol, int crit_mode, T z[8], int *big)
@@ -134,7 +136,16 @@ __device__ __forceinline__ int pivot2x2(T hpp, T hqq, T hpq_re, T hpq_im, T spp,
         z12r = (e1r * ar - e1i * ai) * it;    z12i = (e1r * ai + e1i * ar) * it;
         z21r = -(e1r * br + e1i * bi) * it;   z21i = -(e1r * bi - e1i * br) * it;
         z22r = cpsi * it;                     z22i = zero;
-        *big = !(cphi == one && cpsi == one);   // Section 6.1.7
+        if (sizeof(T) == sizeof(double)) {
+            *big = !(cphi == one && cpsi == one);   // Section 6.1.7
+        } else {
+            // FP32 parameters (complex64 sweeps): classify as the FP64 test
+            // would; cos^2(phi) = 1 - sin^2(phi) rounds to 1 in FP64 iff
+            // sin(phi) < 2^-27 (about); sin(phi) and sin(psi) are
+            // |ar + i ai| and |br + i bi|, accurate in FP32
+            const T thr = T(7.450580596923828e-09);
+            *big = hyp(ar, ai) >= thr || hyp(br, bi) >= thr;
+        }
     }
     // Z' = D0^ Z^.
     z[0] = dp * z11r; z[1] = dp * z11i; z[2] = dp * z12r; z[3] = dp * z12i;
