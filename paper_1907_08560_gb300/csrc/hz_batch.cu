@@ -425,9 +425,9 @@ static cudaError_t enqueue_tick(const BatchBuffers &bb, const Plan &pl, int batc
     for (const PlanP &q : pl.pp) kkmax = std::max(kkmax, q.kk);
     const int gthreads = hz::gram_threads(kkmax);
     hz::gram_batched<<<pl.gram_work, gthreads, 0, st>>>(bb.d_pen, bb.d_state, wg);
-    hz::inner_batched<<<pl.inner_work, 1024, 3 * sizeof(double2) * hz::KKMAX * hz::KKMAX, st>>>(
+    hz::inner_batched<<<pl.inner_work, 1024, hz::inner_smem_bytes(sizeof(double2)), st>>>(
         bb.d_pen, bb.d_state, wi, inner_sweeps, crit_mode);
-    hz::update_batched<<<pl.update_work, 256, 2 * sizeof(double2) * hz::KKMAX * hz::KKMAX, st>>>(
+    hz::update_batched<<<pl.update_work, 256, hz::update_smem(sizeof(double2)), st>>>(
         bb.d_pen, bb.d_state, wu);
     hz::control_batched<<<1, 128, 0, st>>>(bb.d_pen, bb.d_state, batch, max_sweeps, bb.d_hist,
                                            kHistLen, bb.d_active);
@@ -437,10 +437,10 @@ static cudaError_t enqueue_tick(const BatchBuffers &bb, const Plan &pl, int batc
 static cudaError_t batch_attributes()
 {
     cudaError_t e = cudaFuncSetAttribute(hz::inner_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(3 * sizeof(double2) * hz::KKMAX * hz::KKMAX));
+                                         (int)hz::inner_smem_bytes(sizeof(double2)));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(hz::update_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(2 * sizeof(double2) * hz::KKMAX * hz::KKMAX));
+                                (int)hz::update_smem(sizeof(double2)));
 }
 
 // Run ticks until no pencil is active: a graph of `ticks_per_graph` ticks is

@@ -27,7 +27,7 @@ __device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict_
 {
     using T2 = typename cplx<T>::t;
     using U = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
-    __shared__ T2 xs[GRAM_KT][KKMAX];
+    __shared__ T2 xs[GRAM_KT][KKMAX + 1];   // padded: the staging stores walk down rows
     __shared__ U sgn[GRAM_KT];
     __shared__ int cols[KKMAX];
     const int tid = threadIdx.x, nthr = blockDim.x;

@@ -95,9 +95,11 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
 {
     using U2 = typename cplx<TU>::t;
     using X = InnerSync<CL>;
-    U2 *H = reinterpret_cast<U2 *>(smraw_inner);   // [kk * kk], column-major
-    U2 *S = H + KKMAX * KKMAX;
-    U2 *Z = S + KKMAX * KKMAX;
+    // column-major with columns of INNER_LD = KKMAX + 1 entries, so that the
+    // entries of a row (stride one column) fall in different banks
+    U2 *H = reinterpret_cast<U2 *>(smraw_inner);
+    U2 *S = H + KKMAX * INNER_LD;
+    U2 *Z = S + KKMAX * INNER_LD;
     const int crank = X::rank();
     // the CL copies of the block pivot (H^, S^, Z^ are consecutive)
     U2 *copies[CL];
@@ -108,7 +110,7 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
 #pragma unroll
         for (int r = 0; r < CL; ++r) copies[r][off] = v;
     };
-    const int HS = KKMAX * KKMAX;               // offset of S from H (Z: 2 HS)
+    const int HS = KKMAX * INNER_LD;            // offset of S from H (Z: 2 HS)
     __shared__ TU zu[KKMAX / 2][8];          // the step's 2x2 transformations
     __shared__ int tr[KKMAX / 2];            // pivot transformed?
     __shared__ int pslot[KKMAX];             // slots of pivot l: 2l, 2l+1
@@ -142,9 +144,9 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
             hi = 0; si = 0;
             if (!valid[i]) { sr = 1.0; hr = 0.0; }
         }
-        put(i + kk * j, c_make<U2, TU>((TU)hr, (TU)hi));
-        put(HS + i + kk * j, c_make<U2, TU>((TU)sr, (TU)si));
-        put(2 * HS + i + kk * j, c_make<U2, TU>((TU)(i == j ? 1 : 0), (TU)0));
+        put(i + INNER_LD * j, c_make<U2, TU>((TU)hr, (TU)hi));
+        put(HS + i + INNER_LD * j, c_make<U2, TU>((TU)sr, (TU)si));
+        put(2 * HS + i + INNER_LD * j, c_make<U2, TU>((TU)(i == j ? 1 : 0), (TU)0));
     }
     X::sync();
 
@@ -165,9 +167,9 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                     int rc = PIV_NONE, big = 0;
                     TU zl[8];
                     if (valid[pa] && valid[pb]) {
-                        const U2 hab = H[pa + kk * pb], sab = S[pa + kk * pb];
-                        rc = pivot2x2<TU>(H[pa + kk * pa].x, H[pb + kk * pb].x, hab.x, hab.y,
-                                          S[pa + kk * pa].x, S[pb + kk * pb].x, sab.x, sab.y,
+                        const U2 hab = H[pa + INNER_LD * pb], sab = S[pa + INNER_LD * pb];
+                        rc = pivot2x2<TU>(H[pa + INNER_LD * pa].x, H[pb + INNER_LD * pb].x, hab.x, hab.y,
+                                          S[pa + INNER_LD * pa].x, S[pb + INNER_LD * pb].x, sab.x, sab.y,
                                           (TU)a.tol, a.crit_mode, zl, &big);
                     }
                     // complex64 preconditioning sweeps leave a pivot that looks
@@ -210,8 +212,8 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                     const int ab = mat ? HS : 0;
                     const int aI = pslot[2 * I], bI = pslot[2 * I + 1];
                     const int aJ = pslot[2 * Jb], bJ = pslot[2 * Jb + 1];
-                    U2 x00 = A[aI + kk * aJ], x01 = A[aI + kk * bJ];
-                    U2 x10 = A[bI + kk * aJ], x11 = A[bI + kk * bJ];
+                    U2 x00 = A[aI + INNER_LD * aJ], x01 = A[aI + INNER_LD * bJ];
+                    U2 x10 = A[bI + INNER_LD * aJ], x11 = A[bI + INNER_LD * bJ];
                     if (tr[Jb]) {            // right: rows of the block times Z_J
                         c_right<U2, TU>(x00, x01, zu[Jb]);
                         c_right<U2, TU>(x10, x11, zu[Jb]);
@@ -225,23 +227,23 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                         x11.y = 0;
                         x10 = c_make<U2, TU>(x01.x, -x01.y);
                     }
-                    put(ab + aI + kk * aJ, x00); put(ab + aI + kk * bJ, x01);
-                    put(ab + bI + kk * aJ, x10); put(ab + bI + kk * bJ, x11);
+                    put(ab + aI + INNER_LD * aJ, x00); put(ab + aI + INNER_LD * bJ, x01);
+                    put(ab + bI + INNER_LD * aJ, x10); put(ab + bI + INNER_LD * bJ, x11);
                     if (I != Jb) {
-                        put(ab + aJ + kk * aI, c_make<U2, TU>(x00.x, -x00.y));
-                        put(ab + bJ + kk * aI, c_make<U2, TU>(x01.x, -x01.y));
-                        put(ab + aJ + kk * bI, c_make<U2, TU>(x10.x, -x10.y));
-                        put(ab + bJ + kk * bI, c_make<U2, TU>(x11.x, -x11.y));
+                        put(ab + aJ + INNER_LD * aI, c_make<U2, TU>(x00.x, -x00.y));
+                        put(ab + bJ + INNER_LD * aI, c_make<U2, TU>(x01.x, -x01.y));
+                        put(ab + aJ + INNER_LD * bI, c_make<U2, TU>(x10.x, -x10.y));
+                        put(ab + bJ + INNER_LD * bI, c_make<U2, TU>(x11.x, -x11.y));
                     }
                 } else {
                     const int q = it - 2 * nblk;
                     const int row = q % kk, l = q / kk;
                     if (!tr[l]) continue;
                     const int pa = pslot[2 * l], pb = pslot[2 * l + 1];
-                    U2 u = Z[row + kk * pa], w = Z[row + kk * pb];
+                    U2 u = Z[row + INNER_LD * pa], w = Z[row + INNER_LD * pb];
                     c_right<U2, TU>(u, w, zu[l]);
-                    put(2 * HS + row + kk * pa, u);
-                    put(2 * HS + row + kk * pb, w);
+                    put(2 * HS + row + INNER_LD * pa, u);
+                    put(2 * HS + row + INNER_LD * pb, w);
                 }
             }
             X::sync();
@@ -259,7 +261,7 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
     // each CTA of a cluster writes 1/CL of the entries
     for (int idx = tid * CL + crank; idx < kk * kk; idx += CL * blockDim.x) {
         const int i = idx % kk, j = idx / kk;
-        const U2 v = Z[i + kk * j];
+        const U2 v = Z[i + INNER_LD * j];
         zo[i + KKMAX * j] = make_double2((double)v.x, (double)v.y);
     }
     if (tid == 0 && crank == 0) {

@@ -9,6 +9,15 @@ constexpr int KKMAX = 64;          // largest block pivot order 2 wb (wb <= 32)
 constexpr int ROWPAD = 64;         // row padding of each range of W
 constexpr int GRAM_KT = 16;        // rows staged per Gram step
 constexpr int UPD_R = 64;          // rows per update tile
+constexpr int UPD_LD = KKMAX + 1;  // padded row length of the update's shared tiles
+constexpr int INNER_LD = KKMAX + 1;  // padded column length of the inner level's (H^, S^, Z^)
+
+// Dynamic shared memory of an inner-level CTA: H^, S^, Z^ (elem = 16 or 8).
+inline size_t inner_smem_bytes(size_t elem) { return 3 * elem * (size_t)KKMAX * INNER_LD; }
+
+// Dynamic shared memory of an update CTA: Z^ [KKMAX][UPD_LD] and the row tile
+// [UPD_R][UPD_LD] (elem = 16 for complex128, 8 for complex64).
+inline size_t update_smem(size_t elem) { return elem * (size_t)(KKMAX + UPD_R) * UPD_LD; }
 
 // Step descriptor passed by value to every step kernel.
 struct StepArgs {

@@ -489,7 +489,7 @@ cudaError_t launch_gram(const void *W, bool single, const int8_t *Jrow, const St
 
 static size_t inner_smem(bool single)
 {
-    return 3 * (single ? sizeof(float2) : sizeof(double2)) * KKMAX * KKMAX;
+    return inner_smem_bytes(single ? sizeof(float2) : sizeof(double2));
 }
 
 // Cluster widths of the inner level usable on this device (bit CL set: a
@@ -531,10 +531,10 @@ cudaError_t setup_kernels()
                              (int)inner_smem(true));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(update_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(2 * sizeof(double2) * KKMAX * KKMAX));
+                             (int)update_smem(sizeof(double2)));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(update_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(2 * sizeof(float2) * KKMAX * KKMAX));
+                             (int)update_smem(sizeof(float2)));
     if (e != cudaSuccess) return e;
     if (g_cluster_mask < 0) {
         int m64 = 0, m32 = 0;
@@ -611,10 +611,10 @@ cudaError_t launch_update(void *W, bool single, const StepArgs &a, const double2
     const long long Mt = (long long)a.m_pad + a.p_pad + a.n_pad;
     dim3 grid((unsigned)(Mt / UPD_R), a.npairs);
     if (single)
-        update_kernel<float, double><<<grid, 256, 2 * sizeof(float2) * KKMAX * KKMAX, s>>>(
+        update_kernel<float, double><<<grid, 256, update_smem(sizeof(float2)), s>>>(
             (float2 *)W, a, zhat, pair_flag);
     else
-        update_kernel<double, double><<<grid, 256, 2 * sizeof(double2) * KKMAX * KKMAX, s>>>(
+        update_kernel<double, double><<<grid, 256, update_smem(sizeof(double2)), s>>>(
             (double2 *)W, a, zhat, pair_flag);
     return cudaGetLastError();
 }

@@ -18,8 +18,10 @@ __device__ __forceinline__ void update_body(typename cplx<T>::t *__restrict__ W,
                                             unsigned char *smraw)
 {
     using T2 = typename cplx<T>::t;
-    T2 *zs = reinterpret_cast<T2 *>(smraw);          // [KKMAX][KKMAX] row l, col j
-    T2 *xs = zs + KKMAX * KKMAX;                      // [UPD_R][KKMAX]
+    // rows padded to UPD_LD: the transposed stores of Z^ and of the row tile
+    // (consecutive threads on consecutive rows) then hit distinct banks
+    T2 *zs = reinterpret_cast<T2 *>(smraw);          // [KKMAX][UPD_LD] row l, col j
+    T2 *xs = zs + KKMAX * UPD_LD;                     // [UPD_R][UPD_LD]
     __shared__ int cols[KKMAX];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     if (tid < KKMAX) cols[tid] = tid < kk ? slot[tid] : -1;
@@ -28,7 +30,7 @@ __device__ __forceinline__ void update_body(typename cplx<T>::t *__restrict__ W,
         T2 v;
         if (l < kk && j < kk) { v.x = (T)zp[l + KKMAX * j].x; v.y = (T)zp[l + KKMAX * j].y; }
         else { v.x = 0; v.y = 0; }
-        zs[l * KKMAX + j] = v;
+        zs[l * UPD_LD + j] = v;
     }
     __syncthreads();
     for (int idx = tid; idx < UPD_R * KKMAX; idx += 256) {
@@ -37,7 +39,7 @@ __device__ __forceinline__ void update_body(typename cplx<T>::t *__restrict__ W,
         T2 v;
         if (col >= 0) v = W[(long long)col * ld + row0 + r];
         else { v.x = 0; v.y = 0; }
-        xs[r * KKMAX + s] = v;
+        xs[r * UPD_LD + s] = v;
     }
     __syncthreads();
     T accr[4][4], acci[4][4];
@@ -48,9 +50,9 @@ __device__ __forceinline__ void update_body(typename cplx<T>::t *__restrict__ W,
     for (int l = 0; l < kk; ++l) {
         T2 x[4], z[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) x[i] = xs[(ty + 16 * i) * KKMAX + l];
+        for (int i = 0; i < 4; ++i) x[i] = xs[(ty + 16 * i) * UPD_LD + l];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) z[j] = zs[l * KKMAX + tx + 16 * j];
+        for (int j = 0; j < 4; ++j) z[j] = zs[l * UPD_LD + tx + 16 * j];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -69,13 +71,13 @@ __device__ __forceinline__ void update_body(typename cplx<T>::t *__restrict__ W,
             T2 v;
             v.x = accr[i][j];
             v.y = acci[i][j];
-            xs[(ty + 16 * i) * KKMAX + tx + 16 * j] = v;
+            xs[(ty + 16 * i) * UPD_LD + tx + 16 * j] = v;
         }
     __syncthreads();
     for (int idx = tid; idx < UPD_R * KKMAX; idx += 256) {
         const int r = idx % UPD_R, s = idx / UPD_R;
         const int col = cols[s];
-        if (col >= 0) W[(long long)col * ld + row0 + r] = xs[r * KKMAX + s];
+        if (col >= 0) W[(long long)col * ld + row0 + r] = xs[r * UPD_LD + s];
     }
 }
 
