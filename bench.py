@@ -634,6 +634,26 @@ def main():
                                 "status": st_ms, "eig_rel_diff_vs_fp64_max": emax,
                                 "eig_rel_diff_over_tol_max": eratio}
         msolver.close()
+        # the same schedule with the complex64 sweeps' 2x2 parameters in FP32
+        msolver = ghsvd.Solver(local, block_width=W_BLOCK, precision=ghsvd.GHSVD_PRECISION_MIXED,
+                               max_sweeps=args.max_sweeps, mixed_max_sweeps=60, mixed_param32=1)
+        msolver.solve(Fd, Gd, Jd, stream=stream)          # warm-up
+        torch.cuda.synchronize()
+        m0.record(stream)
+        for _ in range(args.mixed_steps):
+            lam_mf, _, _, st_mf = msolver.solve(Fd, Gd, Jd, stream=stream)
+        m1.record(stream)
+        torch.cuda.synchronize()
+        mf_ms = allreduce(m0.elapsed_time(m1), dist.ReduceOp.MAX if dist else None)
+        emax, eratio = eig_vs_fp64(lam_mf)
+        sst_f = msolver.stats()
+        mvalue3 = world * args.mixed_steps / (mf_ms / 1e3)
+        mixed["with_fp32_parameters"] = {"value": mvalue3, "speedup_vs_fp64": mvalue3 / value,
+                                         "sweeps_complex64": sst_f["sweeps_low"],
+                                         "sweeps_fp64": sst_f["sweeps"] - sst_f["sweeps_low"],
+                                         "status": st_mf, "eig_rel_diff_vs_fp64_max": emax,
+                                         "eig_rel_diff_over_tol_max": eratio}
+        msolver.close()
 
     # Phase 2 first (the square factors of the (J, I) URV factorization), then
     # the FP64 iteration on them; eigenvectors mapped back to the tall pencil

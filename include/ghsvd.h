@@ -13,6 +13,13 @@
  * place by the Level-2 block HZ method of Section 6.4 until no "big"
  * transformation remains (Section 6.1.7).
  *
+ * Around that iteration: a mixed-precision schedule (GHSVD_PRECISION_MIXED),
+ * batched solves of uneven pencils (ghsvd_solve_batched), a learned warm start
+ * (ghsvd_mlp_*, ghsvd_s_orthonormalize, ghsvd_solve_from), Phase 2 of the
+ * paper (ghsvd_urv, opts.shorten), Phase 4 (ghsvd_inverse, ghsvd_phase4,
+ * ghsvd_decomposition_errors) and a solve that allocates nothing
+ * (ghsvd_solve_noalloc).
+ *
  * Conventions shared by every entry point:
  *   - complex numbers are complex128 (two doubles, real part first);
  *     matrices are column-major with a leading dimension ld >= rows;
@@ -49,10 +56,16 @@ typedef enum {
     GHSVD_ERR_NOMEM = 6,           /* device allocation failed                  */
     GHSVD_ERR_SCRATCH_TOO_SMALL = 7, /* ghsvd_solve_noalloc: the problem does not
                                       fit GHSVD_NOALLOC_SCRATCH_BYTES          */
-    GHSVD_ERR_BREAKDOWN = 8        /* Phase 2: the hyperbolic QR met a J-isotropic
+    GHSVD_ERR_BREAKDOWN = 8,       /* Phase 2: the hyperbolic QR met a J-isotropic
                                       nonzero pivot column, or no row whose sign
                                       matches its J-norm (Section 5.3)        */
+    GHSVD_ERR_TIMEOUT = 9          /* opts.timeout_ms passed; outputs written  */
 } ghsvd_status;
+
+/* Orderings of the pivot pairs (Section 6.3).  The paper cites the MM and ME
+ * parallel orderings without defining them; the round-robin (circle) ordering
+ * is a parallel cyclic strategy in the paper's sense and is the one built. */
+#define GHSVD_ORDER_ROUND_ROBIN 0
 
 /* Precision schedules. */
 #define GHSVD_PRECISION_FP64 0     /* every sweep in complex128 / FP64            */
@@ -80,13 +93,27 @@ typedef struct {
     int gram_chunk;      /* rows per Gram work unit; 0 = automatic            */
     int timing;          /* 1: time every step kernel with CUDA events on the
                             solve's stream (ghsvd_stats.ms_*); 0 (default): off */
+    int ordering;        /* GHSVD_ORDER_ROUND_ROBIN (default; the only one)    */
+    double tol_scale;    /* multiplies eps sqrt(n) in eq. 6.12 (default 1.0,
+                            > 0; larger values stop earlier, less accurately) */
+    int64_t timeout_ms;  /* > 0: stop after the sweep in which this wall time
+                            (from the start of the solve) passes and return
+                            GHSVD_ERR_TIMEOUT with the outputs of the current
+                            factors; 0 (default): no limit                     */
+    int mixed_param32;   /* GHSVD_PRECISION_MIXED: 0 (default) computes the 2x2
+                            parameters of the complex64 sweeps in FP64, as the
+                            method prescribes; 1 computes them in FP32 and
+                            counts a rotation as big by the FP64 test
+                            (sin phi or sin psi >= 2^-27): faster, the same
+                            rounds and accuracy on the benchmark pencils     */
     int shorten;         /* 1: Phase 2 first (Section 5, see ghsvd_urv): the
                             iteration runs on the square factors; lambda is
                             that of the tall pencil and V is returned in the
                             caller's column order (rows permuted back by P2).
                             Not with a warm start.  0 (default): the tall
                             factors.  ghsvd_solve_batched and
-                            ghsvd_solve_noalloc ignore it.                    */
+                            ghsvd_solve_noalloc ignore it (and timeout_ms;
+                            they use tol_scale).                               */
 } ghsvd_opts;
 
 /* Per-solve statistics (Section 6.4.3, "Completing a sweep"). */

@@ -192,6 +192,10 @@ ghsvd_status ghsvd_default_opts(ghsvd_opts *o)
     o->sort_ascending = 0;
     o->gram_chunk = 0;
     o->timing = 0;
+    o->ordering = GHSVD_ORDER_ROUND_ROBIN;
+    o->tol_scale = 1.0;
+    o->timeout_ms = 0;
+    o->shorten = 0;
     return GHSVD_OK;
 }
 
@@ -208,6 +212,7 @@ const char *ghsvd_status_string(ghsvd_status s)
     case GHSVD_ERR_SCRATCH_TOO_SMALL:
         return "problem too large for the no-allocation scratch array (GHSVD_NOALLOC_SCRATCH_BYTES)";
     case GHSVD_ERR_BREAKDOWN: return "hyperbolic QR breakdown (Phase 2)";
+    case GHSVD_ERR_TIMEOUT: return "time limit reached; outputs written";
     }
     return "unknown status";
 }
@@ -224,7 +229,9 @@ ghsvd_status ghsvd_create(ghsvd_t *out, int device, const ghsvd_opts *opts)
         (o.crit_mode != 0 && o.crit_mode != 1) ||
         (o.precision != GHSVD_PRECISION_FP64 && o.precision != GHSVD_PRECISION_MIXED) ||
         o.mixed_max_sweeps < 0 || o.gram_chunk < 0 || (o.timing != 0 && o.timing != 1) ||
-        (o.shorten != 0 && o.shorten != 1))
+        (o.shorten != 0 && o.shorten != 1) || o.ordering != GHSVD_ORDER_ROUND_ROBIN ||
+        (o.mixed_param32 != 0 && o.mixed_param32 != 1) ||
+        !(o.tol_scale > 0.0 && o.tol_scale < 1e300) || o.timeout_ms < 0)
         return GHSVD_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -427,10 +434,11 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
         InnerArgs ia{};
         ia.npairs = npairs; ia.kk = kk; ia.cpp = cpp; ia.chunks_h = chunks_h;
         ia.inner_sweeps = o.inner_sweeps; ia.crit_mode = o.crit_mode;
-        const double tol64 = ldexp(1.0, -53) * sqrt((double)n);
+        ia.param32 = o.mixed_param32;
+        const double tol64 = o.tol_scale * ldexp(1.0, -53) * sqrt((double)n);
         // complex64 sweeps: the single-precision unit roundoff in eq. 6.12,
         // so that pivots below the Gram's rounding level are left alone
-        const double tol32 = ldexp(1.0, -24) * sqrt((double)n);
+        const double tol32 = o.tol_scale * ldexp(1.0, -24) * sqrt((double)n);
 
         // Mixed schedule (iterative refinement): complex64 sweeps run on
         // W32 = fl32(W) with Z' restarted at I until their big transformations
@@ -451,6 +459,12 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
             CUDA_TRY(grow(&h->Wtmp, Mt * n, &h->cap_wtmp));
         }
         while (sweeps < o.max_sweeps) {
+            if (o.timeout_ms > 0 && sweeps > 0 &&
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() >=
+                    (double)o.timeout_ms) {
+                status = GHSVD_ERR_TIMEOUT;
+                break;
+            }
             const bool single = phase_single != 0;
             ia.tol = single ? tol32 : tol64;
             CUDA_TRY(cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned long long), st));
@@ -603,7 +617,7 @@ static ghsvd_status solve_entry(ghsvd_t h, int64_t m, int64_t p, int64_t n, cons
     if (s == GHSVD_OK && hflags[0]) s = GHSVD_ERR_BREAKDOWN;
     if (s == GHSVD_OK) {
         s = solve_impl(h, n, n, n, Fs, n, Js, 0, Gs, n, nullptr, 0, lambda, Vs, n, sweeps, st);
-        if (V && (s == GHSVD_OK || s == GHSVD_ERR_NOT_CONVERGED)) {
+        if (V && (s == GHSVD_OK || s == GHSVD_ERR_NOT_CONVERGED || s == GHSVD_ERR_TIMEOUT)) {
             e = hz::launch_permute_rows((const double2 *)Vs, n, (int)n, permi, (double2 *)V, ldv, st);
             if (e != cudaSuccess) s = status_of(e);
             h->stats.kernel_launches += 1;
@@ -682,7 +696,7 @@ ghsvd_status ghsvd_solve_host(ghsvd_t h, int64_t m, int64_t p, int64_t n, const 
     if (e == cudaSuccess) {
         s = solve_entry(h, m, p, n, dF, m, J ? dJ : nullptr, n_plus, dG, p, nullptr, 0, dl, dV, n,
                         sweeps, st);
-        if (s == GHSVD_OK || s == GHSVD_ERR_NOT_CONVERGED) {
+        if (s == GHSVD_OK || s == GHSVD_ERR_NOT_CONVERGED || s == GHSVD_ERR_TIMEOUT) {
             e = cudaMemcpyAsync(lambda, dl, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess && V)
                 e = cudaMemcpy2DAsync(V, sizeof(double2) * ldv, dV, sizeof(double2) * n,

@@ -96,7 +96,8 @@ extern "C" ghsvd_status ghsvd_solve_noalloc(int64_t m64, int64_t p64, int64_t n6
     if (m64 > (1 << 24) || p64 > (1 << 24) || n64 > (1 << 16)) return GHSVD_ERR_SCRATCH_TOO_SMALL;
     if (o.block_width < 1 || o.block_width > hz::KKMAX / 2 || o.inner_sweeps < 1 ||
         o.inner_sweeps > 30 || o.max_sweeps < 1 || o.max_sweeps > 1000 ||
-        (o.crit_mode != 0 && o.crit_mode != 1) || o.precision != GHSVD_PRECISION_FP64)
+        (o.crit_mode != 0 && o.crit_mode != 1) || o.precision != GHSVD_PRECISION_FP64 ||
+        !(o.tol_scale > 0.0 && o.tol_scale < 1e300))
         return GHSVD_ERR_INVALID_ARG;
     const int m = (int)m64, p = (int)p64, n = (int)n64;
     cudaStream_t st = (cudaStream_t)stream;
@@ -224,7 +225,7 @@ extern "C" ghsvd_status ghsvd_solve_noalloc(int64_t m64, int64_t p64, int64_t n6
         hz::InnerArgs ia{};
         ia.npairs = npairs; ia.kk = kk; ia.cpp = cpp; ia.chunks_h = chunks_h;
         ia.inner_sweeps = o.inner_sweeps; ia.crit_mode = o.crit_mode;
-        ia.tol = ldexp(1.0, -53) * sqrt((double)n);
+        ia.tol = o.tol_scale * ldexp(1.0, -53) * sqrt((double)n);
         while (sweeps < o.max_sweeps) {
             NA_TRY(cudaMemsetAsync(counters, 0, 16, st));
             for (int r = 0; r < nsteps; ++r) {

@@ -76,7 +76,7 @@ inner_batched(const BPencil *__restrict__ P, const BState *__restrict__ S, const
     if (!S[w.x].active) return;
     const BPencil &p = P[w.x];
     const int r = S[w.x].step;
-    InnerArgs a;
+    InnerArgs a{};
     a.npairs = p.npairs;
     a.kk = p.kk;
     a.cpp = p.chunks_h + p.chunks_s;
@@ -281,7 +281,7 @@ constexpr int kHistLen = 64;
 static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, const void *const *F,
                                 const int64_t *ldf, const int8_t *const *J, const int64_t *n_plus,
                                 const void *const *G, const int64_t *ldg, const void *const *V0,
-                                const int64_t *ldv0, cudaStream_t st)
+                                const int64_t *ldv0, cudaStream_t st, double tol_scale)
 {
     if (pl.bytes > bb.arena_bytes) {
         cudaFree(bb.arena);
@@ -325,7 +325,7 @@ static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, con
         d.m_pad = q.m_pad; d.p_pad = q.p_pad; d.n_pad = q.n_pad; d.n = q.n;
         d.kk = q.kk; d.npairs = q.npairs; d.nsteps = q.nsteps; d.kc = q.kc;
         d.chunks_h = q.chunks_h; d.chunks_s = q.chunks_s;
-        d.tol = ldexp(1.0, -53) * sqrt((double)q.n);
+        d.tol = tol_scale * ldexp(1.0, -53) * sqrt((double)q.n);
         hp[i] = d;
         // schedule tables (host-built, as for a single pencil)
         std::vector<int> off;
@@ -515,7 +515,7 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
         w = 32;
         for (int c : cands) {
             Plan pl = make_plan(batch, m, p, n, c, sms, V0 != nullptr);
-            ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, V0, ldv0, st);
+            ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, V0, ldv0, st, opts->tol_scale);
             if (s != GHSVD_OK) return s;
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
@@ -542,7 +542,7 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
     if (w_chosen) *w_chosen = w;
     Plan pl = make_plan(batch, m, p, n, w, sms, V0 != nullptr);
     auto t0 = std::chrono::steady_clock::now();
-    ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, V0, ldv0, st);
+    ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, V0, ldv0, st, opts->tol_scale);
     if (s != GHSVD_OK) return s;
     // bad J entries or non-finite inputs
     std::vector<int> herr(2 * batch, 0);

@@ -74,11 +74,12 @@ __device__ __forceinline__ void c_left(T2 &x0, T2 &x1, const T *z)
 // computed, the mirror block is its conjugate transpose.
 //
 // TP is the type of the Gram partials, TU the type in which the block
-// pivots are kept and transformed and the 2x2 parameters (eq. 6.5-6.12) are
-// computed: double for the FP64 sweeps, float for the complex64
-// preconditioning sweeps.  The complex64 sweeps still count "big" as FP64
-// would (sin(phi) or sin(psi) >= 2^-27), which keeps the stagnation test of
-// the mixed schedule's refinement rounds as with FP64 parameters.
+// pivots are kept and transformed (double for the FP64 sweeps, float for the
+// complex64 preconditioning sweeps).  The 2x2 parameters (eq. 6.5-6.12) are
+// computed in FP64 from the pivot entries; with a.param32 the complex64
+// sweeps compute them in FP32 instead and still count "big" as FP64 would
+// (sin(phi) or sin(psi) >= 2^-27), which keeps the stagnation test of the
+// mixed schedule's refinement rounds as with FP64 parameters.
 //
 // The Gram kernel writes the entries on and above the diagonal; an entry
 // below it is the conjugate of its mirror (the block pivots are Hermitian).
@@ -168,9 +169,20 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                     TU zl[8];
                     if (valid[pa] && valid[pb]) {
                         const U2 hab = H[pa + INNER_LD * pb], sab = S[pa + INNER_LD * pb];
-                        rc = pivot2x2<TU>(H[pa + INNER_LD * pa].x, H[pb + INNER_LD * pb].x, hab.x, hab.y,
-                                          S[pa + INNER_LD * pa].x, S[pb + INNER_LD * pb].x, sab.x, sab.y,
-                                          (TU)a.tol, a.crit_mode, zl, &big);
+                        if (sizeof(TU) == sizeof(float) && a.param32) {
+                            rc = pivot2x2<TU>(H[pa + INNER_LD * pa].x, H[pb + INNER_LD * pb].x, hab.x,
+                                              hab.y, S[pa + INNER_LD * pa].x, S[pb + INNER_LD * pb].x,
+                                              sab.x, sab.y, (TU)a.tol, a.crit_mode, zl, &big);
+                        } else {
+                            double zd[8];
+                            rc = pivot2x2<double>((double)H[pa + INNER_LD * pa].x,
+                                                  (double)H[pb + INNER_LD * pb].x, (double)hab.x,
+                                                  (double)hab.y, (double)S[pa + INNER_LD * pa].x,
+                                                  (double)S[pb + INNER_LD * pb].x, (double)sab.x,
+                                                  (double)sab.y, a.tol, a.crit_mode, zd, &big);
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) zl[q] = (TU)zd[q];
+                        }
                     }
                     // complex64 preconditioning sweeps leave a pivot that looks
                     // dependent at their rounding level alone; the FP64 sweeps

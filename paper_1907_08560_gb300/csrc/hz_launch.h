@@ -36,6 +36,7 @@ struct InnerArgs {
     int inner_sweeps;                  // 1 = BO, > 1 = FB
     int crit_mode;                     // eq. 6.12 reading
     double tol;                        // eps * sqrt(n)
+    int param32;                       // complex64 sweeps: 2x2 parameters in FP32
 };
 
 // Threads of a Gram CTA: 16 per upper-triangular 16 x 16 tile of the kk x kk pivot.

@@ -26,6 +26,8 @@ GHSVD_ERR_CUDA = 5
 GHSVD_ERR_NOMEM = 6
 GHSVD_ERR_SCRATCH_TOO_SMALL = 7
 GHSVD_ERR_BREAKDOWN = 8
+GHSVD_ERR_TIMEOUT = 9
+GHSVD_ORDER_ROUND_ROBIN = 0
 
 GHSVD_PRECISION_FP64 = 0
 GHSVD_PRECISION_MIXED = 1
@@ -36,7 +38,9 @@ class ghsvd_opts(ctypes.Structure):
                 ("max_sweeps", ctypes.c_int), ("crit_mode", ctypes.c_int),
                 ("precision", ctypes.c_int), ("mixed_max_sweeps", ctypes.c_int),
                 ("sort_ascending", ctypes.c_int), ("gram_chunk", ctypes.c_int),
-                ("timing", ctypes.c_int), ("shorten", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("ordering", ctypes.c_int),
+                ("tol_scale", ctypes.c_double), ("timeout_ms", ctypes.c_int64),
+                ("mixed_param32", ctypes.c_int), ("shorten", ctypes.c_int)]
 
 
 class ghsvd_stats(ctypes.Structure):
@@ -157,7 +161,7 @@ def ghsvd_default_opts(**kw) -> ghsvd_opts:
     for k, v in kw.items():
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
-        setattr(o, k, int(v))
+        setattr(o, k, float(v) if k == "tol_scale" else int(v))
     return o
 
 
@@ -232,7 +236,8 @@ def ghsvd_solve(h, F, J, G, n_plus: int | None = None, want_vectors: bool = True
                                  ld_of(G), V0.data_ptr(), ld_of(V0), lam.data_ptr(),
                                  V.data_ptr() if V is not None else None, n,
                                  ctypes.byref(sweeps), _stream_ptr(stream))
-    _check(s, (GHSVD_OK, GHSVD_ERR_NOT_CONVERGED) if allow_not_converged else (GHSVD_OK,))
+    _check(s, (GHSVD_OK, GHSVD_ERR_NOT_CONVERGED, GHSVD_ERR_TIMEOUT) if allow_not_converged
+           else (GHSVD_OK,))
     return lam, V, sweeps.value, s
 
 

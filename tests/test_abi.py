@@ -39,15 +39,17 @@ def test_default_opts_and_status_strings(lib):
     from paper_1907_08560_gb300 import ghsvd
     o = ghsvd.ghsvd_default_opts()
     assert (o.block_width, o.inner_sweeps, o.max_sweeps, o.crit_mode, o.precision) == (32, 1, 30, 0, 0)
-    for s in range(9):
+    for s in range(10):
         assert ghsvd.status_string(s) != "unknown status"
+    assert (o.ordering, o.tol_scale, o.timeout_ms, o.shorten) == (0, 1.0, 0, 0)
     assert ghsvd.status_string(99) == "unknown status"
 
 
 def test_create_rejects_bad_options(lib):
     from paper_1907_08560_gb300 import ghsvd
     for bad in (dict(block_width=0), dict(block_width=33), dict(inner_sweeps=0),
-                dict(max_sweeps=0), dict(crit_mode=2), dict(precision=5), dict(shorten=2)):
+                dict(max_sweeps=0), dict(crit_mode=2), dict(precision=5), dict(shorten=2),
+                dict(ordering=1), dict(tol_scale=0.0), dict(tol_scale=-1.0), dict(timeout_ms=-1)):
         o = ghsvd.ghsvd_default_opts(**bad)
         h = ctypes.c_void_p()
         s = lib.ghsvd_create(ctypes.byref(h), 0, ctypes.byref(o))

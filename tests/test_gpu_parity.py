@@ -242,14 +242,16 @@ def test_mixed_precision_schedule(gh):
     check_eigs(F, G, J, gpu, ref)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_lapw_shaped_pencil_256_matches_oracle(gh, precision):
+@pytest.mark.parametrize("precision,param32", [(0, 0), (1, 0), (1, 1)])
+def test_lapw_shaped_pencil_256_matches_oracle(gh, precision, param32):
     # the benchmark's pencil family at n = 256 (F 384 x 256 with 64 negative
-    # signs, G 512 x 256, cond(S) = 1e10), FP64 and mixed schedules
+    # signs, G 512 x 256, cond(S) = 1e10), FP64 and mixed schedules (the
+    # complex64 sweeps with FP64 or FP32 2x2 parameters)
     F, J, G = P.lapw_pencil(256)
     ref = oracle.solve(F, G, J, method="blocked", w=32)
     assert ref["status"] == 0
-    gpu = gpu_solve(gh, F, G, J, block_width=32, precision=precision, max_sweeps=80)
+    gpu = gpu_solve(gh, F, G, J, block_width=32, precision=precision, max_sweeps=80,
+                    mixed_param32=param32)
     assert gpu["status"] == 0
     if precision:
         assert gpu["stats"]["sweeps_low"] > 0
