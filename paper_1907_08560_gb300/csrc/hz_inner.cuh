@@ -76,10 +76,12 @@ __device__ __forceinline__ void c_left(T2 &x0, T2 &x1, const T *z)
 // TP is the type of the Gram partials, TU the type in which the block
 // pivots are kept and transformed (double for the FP64 sweeps, float for the
 // complex64 preconditioning sweeps).  The 2x2 parameters (eq. 6.5-6.12) are
-// computed in FP64 from the pivot entries; with a.param32 the complex64
-// sweeps compute them in FP32 instead and still count "big" as FP64 would
-// (sin(phi) or sin(psi) >= 2^-27), which keeps the stagnation test of the
-// mixed schedule's refinement rounds as with FP64 parameters.
+// computed in FP64 from the pivot entries: correctly rounded step by step in
+// the FP64 sweeps (pivot2x2), with shared reciprocals in the complex64 sweeps
+// (pivot2x2_fast); with a.param32 the complex64 sweeps compute them in FP32
+// instead.  The complex64 sweeps count "big" by the FP64 test (sin(phi) or
+// sin(psi) >= 2^-27), which keeps the stagnation test of the mixed
+// schedule's refinement rounds as with exact FP64 parameters.
 //
 // The Gram kernel writes the entries on and above the diagonal; an entry
 // below it is the conjugate of its mirror (the block pivots are Hermitian).
@@ -173,6 +175,15 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                             rc = pivot2x2<TU>(H[pa + INNER_LD * pa].x, H[pb + INNER_LD * pb].x, hab.x,
                                               hab.y, S[pa + INNER_LD * pa].x, S[pb + INNER_LD * pb].x,
                                               sab.x, sab.y, (TU)a.tol, a.crit_mode, zl, &big);
+                        } else if (sizeof(TU) == sizeof(float)) {
+                            double zd[8];
+                            rc = pivot2x2_fast((double)H[pa + INNER_LD * pa].x,
+                                               (double)H[pb + INNER_LD * pb].x, (double)hab.x,
+                                               (double)hab.y, (double)S[pa + INNER_LD * pa].x,
+                                               (double)S[pb + INNER_LD * pb].x, (double)sab.x,
+                                               (double)sab.y, a.tol, a.crit_mode, zd, &big);
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) zl[q] = (TU)zd[q];
                         } else {
                             double zd[8];
                             rc = pivot2x2<double>((double)H[pa + INNER_LD * pa].x,

@@ -153,6 +153,78 @@ __device__ __forceinline__ int pivot2x2(T hpp, T hqq, T hpq_re, T hpq_im, T spp,
     return PIV_TRANSFORM;
 }
 
+// The same 2x2 transformation with FP64 parameters for the complex64 sweeps
+// of the mixed schedule: the formulas of pivot2x2 with one reciprocal shared
+// by the divisions by the same quantity, reciprocal square roots for D0 and
+// plain sqrt(a^2 + b^2) (errors of a few FP64 ulps, far below the complex64
+// data the parameters are applied to), and "big" decided by
+// sin(phi), sin(psi) >= 2^-27, the FP64 test on a cosine rounding to 1.
+__device__ __forceinline__ int pivot2x2_fast(double hpp, double hqq, double hpq_re, double hpq_im,
+                                             double spp, double sqq, double spq_re, double spq_im,
+                                             double tol, int crit_mode, double z[8], int *big)
+{
+    *big = 0;
+    if (!(spp > 0.0) || !(sqq > 0.0)) return PIV_ERR_RANK;
+    if (!isfinite(hpp) || !isfinite(hqq) || !isfinite(hpq_re) || !isfinite(hpq_im) ||
+        !isfinite(spp) || !isfinite(sqq) || !isfinite(spq_re) || !isfinite(spq_im))
+        return PIV_ERR_NONFINITE;
+    const double dp = rsqrt(spp), dq = rsqrt(sqq);       // Section 6.1.1
+    const double dpq = dp * dq;
+    const double h11 = hpp * dp * dp, h22 = hqq * dq * dq;
+    const double h12r = hpq_re * dpq, h12i = hpq_im * dpq;
+    const double s12r = spq_re * dpq, s12i = spq_im * dpq;
+    const double a1 = fabs(h11), a2 = fabs(h22);
+    const double hmax = fmax(a1, a2), hmin = fmin(a1, a2);
+    const double ah12 = sqrt(h12r * h12r + h12i * h12i);
+    const double x = sqrt(s12r * s12r + s12i * s12i);
+    const bool crit_h = crit_mode == 0 ? ah12 >= (sqrt(hmax) * tol) * sqrt(hmin)
+                                       : ah12 >= (hmax * tol) * hmin;
+    if (!crit_h && !(x >= tol)) return PIV_NONE;            // eq. 6.12
+    if (h12r == 0.0 && h12i == 0.0 && s12r == 0.0 && s12i == 0.0) return PIV_NONE;
+    if (!(x < 1.0)) return PIV_ERR_RANK;
+    double e1r = 1.0, e1i = 0.0;                            // Section 6.1.2
+    if (x != 0.0) { const double ix = 1.0 / x; e1r = s12r * ix; e1i = s12i * ix; }
+    const double t = sqrt((1.0 - x) * (1.0 + x));
+    const double u = e1r * h12r + e1i * h12i;              // eq. 6.5
+    const double v = e1r * h12i - e1i * h12r;
+    const double h = h22 - h11;
+    double z11r, z11i, z12r, z12i, z21r, z21i, z22r, z22i;
+    if (h == 0.0 && v == 0.0) {                             // Section 6.1.6
+        const double c = 0.70710678118654752440;
+        const double d1 = rsqrt(1.0 + x), d2 = rsqrt(1.0 - x);
+        z11r = c * d1;        z11i = 0.0;
+        z12r = -e1r * c * d2; z12i = -e1i * c * d2;
+        z21r = e1r * c * d1;  z21i = -e1i * c * d1;
+        z22r = c * d2;        z22i = 0.0;
+        *big = 1;
+    } else {
+        const double sigma = h >= 0.0 ? 1.0 : -1.0;        // eq. 6.6
+        const double hv = sqrt(h * h + 4.0 * v * v), ihv = 1.0 / hv;
+        const double num = sigma * (2.0 * u - (h11 + h22) * x);   // eq. 6.7
+        const double den = t * hv;
+        const double ir = 1.0 / sqrt(num * num + den * den);
+        const double s2t = num * ir, c2t = den * ir;
+        const double cg = fabs(h) * ihv, sg = sigma * 2.0 * v * ihv;   // eq. 6.11
+        const double xs = x * s2t, tcc = t * cg * c2t;     // eq. 6.10
+        const double qphi = (1.0 + xs + tcc) * 0.5, qpsi = (1.0 - xs + tcc) * 0.5;
+        const double cphi = sqrt(qphi), cpsi = sqrt(qpsi);
+        const double ip = 0.5 * rsqrt(qpsi), iq = 0.5 * rsqrt(qphi);   // 1/(2 cos psi), 1/(2 cos phi)
+        const double tsc = t * sg * c2t;
+        const double ar = (s2t - x) * ip, ai = tsc * ip;
+        const double br = (s2t + x) * iq, bi = -tsc * iq;
+        const double it = 1.0 / t;
+        z11r = cphi * it;                     z11i = 0.0;
+        z12r = (e1r * ar - e1i * ai) * it;    z12i = (e1r * ai + e1i * ar) * it;
+        z21r = -(e1r * br + e1i * bi) * it;   z21i = -(e1r * bi - e1i * br) * it;
+        z22r = cpsi * it;                     z22i = 0.0;
+        const double thr2 = 5.551115123125783e-17;         // (2^-27)^2
+        *big = ar * ar + ai * ai >= thr2 || br * br + bi * bi >= thr2;
+    }
+    z[0] = dp * z11r; z[1] = dp * z11i; z[2] = dp * z12r; z[3] = dp * z12i;   // Z' = D0^ Z^
+    z[4] = dq * z21r; z[5] = dq * z21i; z[6] = dq * z22r; z[7] = dq * z22i;
+    return PIV_TRANSFORM;
+}
+
 // Round-robin (circle) ordering of N (even) slots, step r, pair k: slot N-1
 // meets slot r; slot (r+k) mod (N-1) meets slot (r-k) mod (N-1); the smaller
 // slot first.  Every pair appears exactly once in N-1 steps (Section 6.3).
