@@ -154,11 +154,12 @@ __device__ __forceinline__ int pivot2x2(T hpp, T hqq, T hpq_re, T hpq_im, T spp,
 }
 
 // The same 2x2 transformation with FP64 parameters for the complex64 sweeps
-// of the mixed schedule: the formulas of pivot2x2 with one reciprocal shared
-// by the divisions by the same quantity, reciprocal square roots for D0 and
-// plain sqrt(a^2 + b^2) (errors of a few FP64 ulps, far below the complex64
-// data the parameters are applied to), and "big" decided by
-// sin(phi), sin(psi) >= 2^-27, the FP64 test on a cosine rounding to 1.
+// of the mixed schedule: the formulas of pivot2x2 with every square root and
+// division taken from one reciprocal square root (sqrt(q) = q rsqrt(q),
+// 1/sqrt(q) = rsqrt(q)), eq. 6.12 compared in squares (errors of a few FP64
+// ulps, far below the complex64 data the parameters are applied to), and
+// "big" decided by sin(phi), sin(psi) >= 2^-27, the FP64 test on a cosine
+// rounding to 1.
 __device__ __forceinline__ int pivot2x2_fast(double hpp, double hqq, double hpq_re, double hpq_im,
                                              double spp, double sqq, double spq_re, double spq_im,
                                              double tol, int crit_mode, double z[8], int *big)
@@ -175,16 +176,22 @@ __device__ __forceinline__ int pivot2x2_fast(double hpp, double hqq, double hpq_
     const double s12r = spq_re * dpq, s12i = spq_im * dpq;
     const double a1 = fabs(h11), a2 = fabs(h22);
     const double hmax = fmax(a1, a2), hmin = fmin(a1, a2);
-    const double ah12 = sqrt(h12r * h12r + h12i * h12i);
-    const double x = sqrt(s12r * s12r + s12i * s12i);
-    const bool crit_h = crit_mode == 0 ? ah12 >= (sqrt(hmax) * tol) * sqrt(hmin)
-                                       : ah12 >= (hmax * tol) * hmin;
-    if (!crit_h && !(x >= tol)) return PIV_NONE;            // eq. 6.12
+    const double ah2 = h12r * h12r + h12i * h12i;          // |h_pq|^2
+    const double x2 = s12r * s12r + s12i * s12i;           // x^2
+    const double ch = crit_mode == 0 ? (hmax * tol) * (hmin * tol) : (hmax * tol) * hmin;
+    const bool crit_h = crit_mode == 0 ? ah2 >= ch : ah2 >= ch * ch;
+    if (!crit_h && !(x2 >= tol * tol)) return PIV_NONE;    // eq. 6.12
     if (h12r == 0.0 && h12i == 0.0 && s12r == 0.0 && s12i == 0.0) return PIV_NONE;
-    if (!(x < 1.0)) return PIV_ERR_RANK;
-    double e1r = 1.0, e1i = 0.0;                            // Section 6.1.2
-    if (x != 0.0) { const double ix = 1.0 / x; e1r = s12r * ix; e1i = s12i * ix; }
-    const double t = sqrt((1.0 - x) * (1.0 + x));
+    if (!(x2 < 1.0)) return PIV_ERR_RANK;
+    double x = 0.0, e1r = 1.0, e1i = 0.0;                  // Section 6.1.2
+    if (x2 != 0.0) {
+        const double ix = rsqrt(x2);
+        x = x2 * ix;
+        e1r = s12r * ix;
+        e1i = s12i * ix;
+    }
+    const double t2 = (1.0 - x) * (1.0 + x);
+    const double it = rsqrt(t2), t = t2 * it;
     const double u = e1r * h12r + e1i * h12i;              // eq. 6.5
     const double v = e1r * h12i - e1i * h12r;
     const double h = h22 - h11;
@@ -199,20 +206,21 @@ __device__ __forceinline__ int pivot2x2_fast(double hpp, double hqq, double hpq_
         *big = 1;
     } else {
         const double sigma = h >= 0.0 ? 1.0 : -1.0;        // eq. 6.6
-        const double hv = sqrt(h * h + 4.0 * v * v), ihv = 1.0 / hv;
+        const double hv2 = h * h + 4.0 * v * v;
+        const double ihv = rsqrt(hv2), hv = hv2 * ihv;
         const double num = sigma * (2.0 * u - (h11 + h22) * x);   // eq. 6.7
         const double den = t * hv;
-        const double ir = 1.0 / sqrt(num * num + den * den);
+        const double ir = rsqrt(num * num + den * den);
         const double s2t = num * ir, c2t = den * ir;
         const double cg = fabs(h) * ihv, sg = sigma * 2.0 * v * ihv;   // eq. 6.11
         const double xs = x * s2t, tcc = t * cg * c2t;     // eq. 6.10
         const double qphi = (1.0 + xs + tcc) * 0.5, qpsi = (1.0 - xs + tcc) * 0.5;
-        const double cphi = sqrt(qphi), cpsi = sqrt(qpsi);
-        const double ip = 0.5 * rsqrt(qpsi), iq = 0.5 * rsqrt(qphi);   // 1/(2 cos psi), 1/(2 cos phi)
+        const double rphi = rsqrt(qphi), rpsi = rsqrt(qpsi);
+        const double cphi = qphi * rphi, cpsi = qpsi * rpsi;
+        const double ip = 0.5 * rpsi, iq = 0.5 * rphi;     // 1/(2 cos psi), 1/(2 cos phi)
         const double tsc = t * sg * c2t;
         const double ar = (s2t - x) * ip, ai = tsc * ip;
         const double br = (s2t + x) * iq, bi = -tsc * iq;
-        const double it = 1.0 / t;
         z11r = cphi * it;                     z11i = 0.0;
         z12r = (e1r * ar - e1i * ai) * it;    z12i = (e1r * ai + e1i * ar) * it;
         z21r = -(e1r * br + e1i * bi) * it;   z21i = -(e1r * bi - e1i * br) * it;
