@@ -17,10 +17,126 @@ namespace hz {
 // diagonal tiles the 4 x 4 blocks below the diagonal are skipped.  J enters as a sign flip of the conjugated factor
 // (an integer xor on the sign bits).
 // ---------------------------------------------------------------------------
+// The tile of one thread: the nt diagonal tiles first (so that warps hold two
+// diagonal tiles or two off-diagonal ones), then the tiles above the diagonal
+// in row-major order.  Returns false for the threads without a tile.
+__device__ __forceinline__ bool gram_tile(int kk, int tile, int &ti, int &tj)
+{
+    const int nt = (kk + 15) >> 4;
+    const int ntiles = nt * (nt + 1) / 2;
+    ti = 0;
+    tj = 0;
+    if (tile >= ntiles) return false;
+    if (tile < nt) {
+        ti = tj = tile;
+    } else {
+        int rem = tile - nt;
+        while (rem >= nt - 1 - ti) { rem -= nt - 1 - ti; ++ti; }
+        tj = ti + 1 + rem;
+    }
+    return true;
+}
+
+// The complex128 body: the three-multiplication form of conj(x) y,
+//   Re = xr yr + xi yi,  Im = (xr - xi)(yr + yi) - xr yr + xi yi,
+// three real FMA chains per entry instead of four (the FP64 pipe bounds this
+// kernel); xr - xi and xr + xi are formed once per staged element.  The error
+// of an entry stays bounded by a small multiple of sum |x||y|, as with the
+// usual product; the diagonal's imaginary parts are not used.
+__device__ __forceinline__ void gram_body_3m(const double2 *__restrict__ W, long long ld,
+                                             const int8_t *__restrict__ Jrow,
+                                             const int *__restrict__ slot, int kk, int r0, int r1,
+                                             bool isH, double2 *__restrict__ out)
+{
+    __shared__ double2 xs[GRAM_KT][KKMAX + 1];   // padded: the staging stores walk down rows
+    __shared__ double xd[GRAM_KT][KKMAX + 1];    // xr - xi
+    __shared__ double xp[GRAM_KT][KKMAX + 1];    // xr + xi
+    __shared__ unsigned long long sgn[GRAM_KT];
+    __shared__ int cols[KKMAX];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lx = tid & 3, ly = (tid >> 2) & 3;
+    int ti, tj;
+    const bool active = gram_tile(kk, tid >> 4, ti, tj);
+    const bool diag = ti == tj;
+    const int qr = 16 * ti, qc = 16 * tj;
+    for (int s = tid; s < KKMAX; s += nthr) cols[s] = s < kk ? slot[s] : -1;
+    const unsigned long long signbit = 1ull << 63;
+
+    double t1[4][4], t2[4][4], t3[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { t1[i][j] = 0; t2[i][j] = 0; t3[i][j] = 0; }
+
+    for (int k0 = r0; k0 < r1; k0 += GRAM_KT) {
+        __syncthreads();
+        for (int e = tid; e < GRAM_KT * KKMAX; e += nthr) {
+            const int r = e % GRAM_KT, s = e / GRAM_KT;
+            const int col = cols[s];
+            double2 v = make_double2(0.0, 0.0);
+            if (col >= 0) v = W[(long long)col * ld + k0 + r];
+            xs[r][s] = v;
+            xd[r][s] = v.x - v.y;
+            xp[r][s] = v.x + v.y;
+        }
+        if (tid < GRAM_KT) sgn[tid] = (isH && Jrow[k0 + tid] < 0) ? signbit : 0ull;
+        __syncthreads();
+        if (!active) continue;
+#pragma unroll 1
+        for (int k = 0; k < GRAM_KT; ++k) {
+            const unsigned long long sb = sgn[k];
+            double2 x[4], y[4];
+            double d[4], p[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                x[i] = xs[k][qr + ly + 4 * i];
+                d[i] = xd[k][qr + ly + 4 * i];
+                x[i].x = __longlong_as_double(__double_as_longlong(x[i].x) ^ sb);
+                x[i].y = __longlong_as_double(__double_as_longlong(x[i].y) ^ sb);
+                d[i] = __longlong_as_double(__double_as_longlong(d[i]) ^ sb);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                y[j] = xs[k][qc + lx + 4 * j];
+                p[j] = xp[k][qc + lx + 4 * j];
+            }
+            if (diag) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = i; j < 4; ++j) {
+                        t1[i][j] = fma(x[i].x, y[j].x, t1[i][j]);
+                        t2[i][j] = fma(x[i].y, y[j].y, t2[i][j]);
+                        t3[i][j] = fma(d[i], p[j], t3[i][j]);
+                    }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        t1[i][j] = fma(x[i].x, y[j].x, t1[i][j]);
+                        t2[i][j] = fma(x[i].y, y[j].y, t2[i][j]);
+                        t3[i][j] = fma(d[i], p[j], t3[i][j]);
+                    }
+            }
+        }
+    }
+    if (!active) return;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int ii = qr + ly + 4 * i, jj = qc + lx + 4 * j;
+            if (ii > jj) continue;
+            out[ii + KKMAX * jj] = make_double2(t1[i][j] + t2[i][j], (t3[i][j] - t1[i][j]) + t2[i][j]);
+        }
+}
+
 // The body, for one (pair, row chunk): rows [r0, r1) of W (ld), the pair's
 // kk slot columns `slot`, J signs applied iff isH; writes the partial to out.
+// The complex64 form uses four real FMA chains per entry.
 template <typename T>
-__device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict__ W, long long ld,
+__device__ __forceinline__ void gram_body_4m(const typename cplx<T>::t *__restrict__ W, long long ld,
                                           const int8_t *__restrict__ Jrow,
                                           const int *__restrict__ slot, int kk, int r0, int r1,
                                           bool isH, typename cplx<T>::t *__restrict__ out)
@@ -31,21 +147,9 @@ __device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict_
     __shared__ U sgn[GRAM_KT];
     __shared__ int cols[KKMAX];
     const int tid = threadIdx.x, nthr = blockDim.x;
-    // tile (ti, tj) of this thread: the nt diagonal tiles first (so that
-    // warps hold two diagonal tiles or two off-diagonal ones), then the
-    // tiles above the diagonal in row-major order
-    const int nt = (kk + 15) >> 4;
-    const int ntiles = nt * (nt + 1) / 2;
-    const int tile = tid >> 4, lx = tid & 3, ly = (tid >> 2) & 3;
-    const bool active = tile < ntiles;
-    int ti = 0, tj = 0;
-    if (active && tile < nt) {
-        ti = tj = tile;
-    } else if (active) {
-        int rem = tile - nt;
-        while (rem >= nt - 1 - ti) { rem -= nt - 1 - ti; ++ti; }
-        tj = ti + 1 + rem;
-    }
+    const int lx = tid & 3, ly = (tid >> 2) & 3;
+    int ti, tj;
+    const bool active = gram_tile(kk, tid >> 4, ti, tj);
     const bool diag = ti == tj;
     const int qr = 16 * ti, qc = 16 * tj;
     for (int s = tid; s < KKMAX; s += nthr) cols[s] = s < kk ? slot[s] : -1;
@@ -128,9 +232,21 @@ __device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict_
         }
 }
 
+template <typename T>
+__device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict__ W, long long ld,
+                                          const int8_t *__restrict__ Jrow,
+                                          const int *__restrict__ slot, int kk, int r0, int r1,
+                                          bool isH, typename cplx<T>::t *__restrict__ out)
+{
+    if constexpr (std::is_same<T, double>::value)
+        gram_body_3m(W, ld, Jrow, slot, kk, r0, r1, isH, out);
+    else
+        gram_body_4m<T>(W, ld, Jrow, slot, kk, r0, r1, isH, out);
+}
+
 // One outer step of one pencil: CTA = (pair, row chunk).
 template <typename T>
-__global__ void __launch_bounds__(160, 3)
+__global__ void __launch_bounds__(160, sizeof(T) == 8 ? 2 : 3)
 gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict__ Jrow,
             StepArgs a, typename cplx<T>::t *__restrict__ partial)
 {

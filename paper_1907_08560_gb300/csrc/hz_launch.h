@@ -16,8 +16,12 @@ constexpr int INNER_LD = KKMAX + 1;  // padded column length of the inner level'
 inline size_t inner_smem_bytes(size_t elem) { return 3 * elem * (size_t)KKMAX * INNER_LD; }
 
 // Dynamic shared memory of an update CTA: Z^ [KKMAX][UPD_LD] and the row tile
-// [UPD_R][UPD_LD] (elem = 16 for complex128, 8 for complex64).
-inline size_t update_smem(size_t elem) { return elem * (size_t)(KKMAX + UPD_R) * UPD_LD; }
+// [UPD_R][UPD_LD] (elem = 16 for complex128, 8 for complex64); the complex128
+// update also keeps the real sums Re + Im of both tiles.
+inline size_t update_smem(size_t elem)
+{
+    return (elem == 16 ? 24 : elem) * (size_t)(KKMAX + UPD_R) * UPD_LD;
+}
 
 // Step descriptor passed by value to every step kernel.
 struct StepArgs {

@@ -223,6 +223,10 @@ __global__ void extract_kernel(const double2 *__restrict__ W, long long ld, int 
 // Used once per solve to apply a starting transformation (warm start) or the
 // transformation accumulated by the complex64 sweeps to the FP64 factors.
 // 64 x 64 output tile per CTA, 16-deep K slices staged in shared memory.
+// The complex products take the three-multiplication form
+//   a b = (ar br - ai bi) + i ((ar + ai)(br + bi) - ar br - ai bi)
+// (three real FMA chains per output; the FP64 pipe bounds this kernel), whose
+// error is bounded entrywise by a small multiple of |A||B| as the usual form's.
 // ----------------------------------------------------------------------------
 template <typename TB>
 __global__ void __launch_bounds__(256)
@@ -231,14 +235,15 @@ gemm_kernel(const double2 *__restrict__ A, long long lda, const TB *__restrict__
 {
     __shared__ double2 as[64][17];
     __shared__ double2 bs[16][64];
+    __shared__ double bq[16][64];     // br + bi
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const long long row0 = (long long)blockIdx.x * 64;
     const int col0 = blockIdx.y * 64;
-    double accr[4][4], acci[4][4];
+    double t1[4][4], t2[4][4], t3[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) { accr[i][j] = 0; acci[i][j] = 0; }
+        for (int j = 0; j < 4; ++j) { t1[i][j] = 0; t2[i][j] = 0; t3[i][j] = 0; }
     for (int k0 = 0; k0 < n; k0 += 16) {
         __syncthreads();
         for (int e = tid; e < 64 * 16; e += 256) {
@@ -253,23 +258,30 @@ gemm_kernel(const double2 *__restrict__ A, long long lda, const TB *__restrict__
                 v = make_double2((double)b.x, (double)b.y);
             }
             bs[k][c] = v;
+            bq[k][c] = v.x + v.y;
         }
         __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
         for (int k = 0; k < 16; ++k) {
             double2 x[4], z[4];
+            double xp[4], zq[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) x[i] = as[ty + 16 * i][k];
+            for (int i = 0; i < 4; ++i) {
+                x[i] = as[ty + 16 * i][k];
+                xp[i] = x[i].x + x[i].y;
+            }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) z[j] = bs[k][tx + 16 * j];
+            for (int j = 0; j < 4; ++j) {
+                z[j] = bs[k][tx + 16 * j];
+                zq[j] = bq[k][tx + 16 * j];
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    accr[i][j] = fma(x[i].x, z[j].x, accr[i][j]);
-                    accr[i][j] = fma(-x[i].y, z[j].y, accr[i][j]);
-                    acci[i][j] = fma(x[i].x, z[j].y, acci[i][j]);
-                    acci[i][j] = fma(x[i].y, z[j].x, acci[i][j]);
+                    t1[i][j] = fma(x[i].x, z[j].x, t1[i][j]);
+                    t2[i][j] = fma(x[i].y, z[j].y, t2[i][j]);
+                    t3[i][j] = fma(xp[i], zq[j], t3[i][j]);
                 }
         }
     }
@@ -278,7 +290,9 @@ gemm_kernel(const double2 *__restrict__ A, long long lda, const TB *__restrict__
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int c = col0 + tx + 16 * j;
-            if (c < n) C[row0 + ty + 16 * i + ldc * c] = make_double2(accr[i][j], acci[i][j]);
+            if (c < n)
+                C[row0 + ty + 16 * i + ldc * c] =
+                    make_double2(t1[i][j] - t2[i][j], (t3[i][j] - t1[i][j]) - t2[i][j]);
         }
 }
 

@@ -9,13 +9,106 @@ namespace hz {
 // rows of F, G and Z' (the paper's three ZGEMMs).  One CTA per (64-row tile,
 // pair); pairs whose inner level applied nothing are skipped.
 // ---------------------------------------------------------------------------
-// The body, for one (pair, 64-row tile): rows [row0, row0 + 64) of W (ld)
-// in the pair's kk slot columns `slot`, times its Z^ `zp` (ld KKMAX).
+// The complex128 body: the three-multiplication form of the complex product,
+//   x z = (xr zr - xi zi) + i ((xr + xi)(zr + zi) - xr zr - xi zi),
+// three real FMA chains per output instead of four (the FP64 pipe bounds this
+// kernel).  Its error is bounded entrywise by a small multiple of |x||z|, as
+// the usual product's is, but the imaginary part of an output is not exact
+// when its column of Z^ is e_j; such columns (untouched by the inner level)
+// are copied instead, so that they stay exactly as they were.
+__device__ __forceinline__ void update_body_3m(double2 *__restrict__ W, long long ld,
+                                               const int *__restrict__ slot, int kk, long long row0,
+                                               const double2 *__restrict__ zp, unsigned char *smraw)
+{
+    double2 *zs = reinterpret_cast<double2 *>(smraw);  // [KKMAX][UPD_LD] row l, col j
+    double2 *xs = zs + KKMAX * UPD_LD;                   // [UPD_R][UPD_LD]
+    double *zsum = reinterpret_cast<double *>(xs + UPD_R * UPD_LD);  // zr + zi
+    double *xsum = zsum + KKMAX * UPD_LD;                // xr + xi
+    __shared__ int cols[KKMAX];
+    __shared__ int ident[KKMAX];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    if (tid < KKMAX) cols[tid] = tid < kk ? slot[tid] : -1;
+    for (int idx = tid; idx < KKMAX * KKMAX; idx += 256) {
+        const int l = idx % KKMAX, j = idx / KKMAX;   // zhat column-major
+        double2 v = make_double2(0.0, 0.0);
+        if (l < kk && j < kk) v = zp[l + KKMAX * j];
+        zs[l * UPD_LD + j] = v;
+        zsum[l * UPD_LD + j] = v.x + v.y;
+    }
+    __syncthreads();
+    if (tid < KKMAX) {
+        int id = 1;
+        for (int l = 0; l < KKMAX; ++l) {
+            const double2 v = zs[l * UPD_LD + tid];
+            id &= (v.x == (l == tid ? 1.0 : 0.0)) & (v.y == 0.0);
+        }
+        ident[tid] = id;
+    }
+    for (int idx = tid; idx < UPD_R * KKMAX; idx += 256) {
+        const int r = idx % UPD_R, s = idx / UPD_R;
+        const int col = cols[s];
+        double2 v = make_double2(0.0, 0.0);
+        if (col >= 0) v = W[(long long)col * ld + row0 + r];
+        xs[r * UPD_LD + s] = v;
+        xsum[r * UPD_LD + s] = v.x + v.y;
+    }
+    __syncthreads();
+    double t1[4][4], t2[4][4], t3[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { t1[i][j] = 0; t2[i][j] = 0; t3[i][j] = 0; }
+    for (int l = 0; l < kk; ++l) {
+        double2 x[4], z[4];
+        double xp[4], zq[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            x[i] = xs[(ty + 16 * i) * UPD_LD + l];
+            xp[i] = xsum[(ty + 16 * i) * UPD_LD + l];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            z[j] = zs[l * UPD_LD + tx + 16 * j];
+            zq[j] = zsum[l * UPD_LD + tx + 16 * j];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                t1[i][j] = fma(x[i].x, z[j].x, t1[i][j]);
+                t2[i][j] = fma(x[i].y, z[j].y, t2[i][j]);
+                t3[i][j] = fma(xp[i], zq[j], t3[i][j]);
+            }
+    }
+    double2 v[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = tx + 16 * j;
+            v[i][j] = ident[c] ? xs[(ty + 16 * i) * UPD_LD + c]
+                               : make_double2(t1[i][j] - t2[i][j], (t3[i][j] - t1[i][j]) - t2[i][j]);
+        }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) xs[(ty + 16 * i) * UPD_LD + tx + 16 * j] = v[i][j];
+    __syncthreads();
+    for (int idx = tid; idx < UPD_R * KKMAX; idx += 256) {
+        const int r = idx % UPD_R, s = idx / UPD_R;
+        const int col = cols[s];
+        if (col >= 0) W[(long long)col * ld + row0 + r] = xs[r * UPD_LD + s];
+    }
+}
+
+// The complex64 body (four real FMA chains per output; the FP32 pipe does
+// not bound it).
 template <typename T, typename TZ>
-__device__ __forceinline__ void update_body(typename cplx<T>::t *__restrict__ W, long long ld,
-                                            const int *__restrict__ slot, int kk, long long row0,
-                                            const typename cplx<TZ>::t *__restrict__ zp,
-                                            unsigned char *smraw)
+__device__ __forceinline__ void update_body_4m(typename cplx<T>::t *__restrict__ W, long long ld,
+                                               const int *__restrict__ slot, int kk, long long row0,
+                                               const typename cplx<TZ>::t *__restrict__ zp,
+                                               unsigned char *smraw)
 {
     using T2 = typename cplx<T>::t;
     // rows padded to UPD_LD: the transposed stores of Z^ and of the row tile
@@ -79,6 +172,20 @@ __device__ __forceinline__ void update_body(typename cplx<T>::t *__restrict__ W,
         const int col = cols[s];
         if (col >= 0) W[(long long)col * ld + row0 + r] = xs[r * UPD_LD + s];
     }
+}
+
+// The body, for one (pair, 64-row tile): rows [row0, row0 + 64) of W (ld)
+// in the pair's kk slot columns `slot`, times its Z^ `zp` (ld KKMAX).
+template <typename T, typename TZ>
+__device__ __forceinline__ void update_body(typename cplx<T>::t *__restrict__ W, long long ld,
+                                            const int *__restrict__ slot, int kk, long long row0,
+                                            const typename cplx<TZ>::t *__restrict__ zp,
+                                            unsigned char *smraw)
+{
+    if constexpr (std::is_same<T, double>::value && std::is_same<TZ, double>::value)
+        update_body_3m(W, ld, slot, kk, row0, zp, smraw);
+    else
+        update_body_4m<T, TZ>(W, ld, slot, kk, row0, zp, smraw);
 }
 
 // One outer step of one pencil: CTA = (64-row tile, pair); pairs whose inner

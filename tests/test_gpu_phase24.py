@@ -86,8 +86,8 @@ def test_shortened_solve_matches_tall_oracle(gh, w, n):
     lam, V, sweeps, st = s.solve(dev(gh, F), dev(gh, G), torch.from_numpy(J).cuda())
     assert st == gh.GHSVD_OK
     lam = lam.cpu().numpy()
-    order = np.argsort(ref["lam"])
-    assert np.all(rel_err(lam, ref["lam"][order]) < tol[order])
+    # rel_err and eig_tol_vec both follow the ascending order of the eigenvalues
+    assert np.all(rel_err(lam, ref["lam"]) < tol)
     # V refers to the caller's columns: G V orthonormal (Q_G is unitary) ...
     V = V.cpu().numpy()
     GV = G @ V
