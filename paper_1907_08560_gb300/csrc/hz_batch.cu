@@ -51,7 +51,7 @@ struct BState {
 // Status codes the control kernel writes (mirror ghsvd_status).
 constexpr int BST_RUNNING = -1;
 
-__global__ void __launch_bounds__(160)
+__global__ void __launch_bounds__(128, 3)
 gram_batched(const BPencil *__restrict__ P, const BState *__restrict__ S, const int4 *__restrict__ work)
 {
     const int4 w = work[blockIdx.x];
@@ -423,7 +423,7 @@ static cudaError_t enqueue_tick(const BatchBuffers &bb, const Plan &pl, int batc
     const int4 *wu = wi + pl.inner_work;
     int kkmax = 2;
     for (const PlanP &q : pl.pp) kkmax = std::max(kkmax, q.kk);
-    const int gthreads = hz::gram_threads(kkmax);
+    const int gthreads = hz::gram_threads_c128(kkmax);
     hz::gram_batched<<<pl.gram_work, gthreads, 0, st>>>(bb.d_pen, bb.d_state, wg);
     hz::inner_batched<<<pl.inner_work, 1024, hz::inner_smem_bytes(sizeof(double2)), st>>>(
         bb.d_pen, bb.d_state, wi, inner_sweeps, crit_mode);

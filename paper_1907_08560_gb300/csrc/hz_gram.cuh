@@ -42,7 +42,17 @@ __device__ __forceinline__ bool gram_tile(int kk, int tile, int &ti, int &tj)
 // three real FMA chains per entry instead of four (the FP64 pipe bounds this
 // kernel); xr - xi and xr + xi are formed once per staged element.  The error
 // of an entry stays bounded by a small multiple of sum |x||y|, as with the
-// usual product; the diagonal's imaginary parts are not used.
+// usual product.
+//
+// The FP64 pipe of a sub-partition spends the same time on a warp instruction
+// whatever its active lanes, so the work is dealt in equal shares per warp:
+// gram_threads_c128(kk) threads, one warp per two of the off-diagonal 16 x 16
+// tiles (4 x 4 strided entries per thread, as in the complex64 body), and one
+// warp for the entries strictly above the diagonal of the nt diagonal tiles:
+// 8 lanes per tile, lane rho holding row rho (columns rho+1..15) and row
+// 14 - rho (columns 15-rho..15), 16 entries (row 7 alone: 8).  The real
+// diagonal sum J |x|^2 is split over every thread: thread t adds the squares
+// of the real (t even) or imaginary (t odd) parts of column t / 2.
 __device__ __forceinline__ void gram_body_3m(const double2 *__restrict__ W, long long ld,
                                              const int8_t *__restrict__ Jrow,
                                              const int *__restrict__ slot, int kk, int r0, int r1,
@@ -54,19 +64,36 @@ __device__ __forceinline__ void gram_body_3m(const double2 *__restrict__ W, long
     __shared__ unsigned long long sgn[GRAM_KT];
     __shared__ int cols[KKMAX];
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int lx = tid & 3, ly = (tid >> 2) & 3;
-    int ti, tj;
-    const bool active = gram_tile(kk, tid >> 4, ti, tj);
-    const bool diag = ti == tj;
-    const int qr = 16 * ti, qc = 16 * tj;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nt = (kk + 15) >> 4;
+    const bool dwarp = warp == (nthr >> 5) - 1;  // the diagonal tiles' warp
+    // off-diagonal tile: rows qr + ly + 4i, columns qc + lx + 4j
+    const int ly = (tid >> 2) & 3, lx = tid & 3;
+    int qr = 0, qc = 0;
+    bool active;
+    // diagonal tile: base db, lane rho, its two rows ra, rb; slots s < split
+    // take row ra and column db + rho + 1 + s, the others row rb, column db + s
+    const int rho = lane & 7, db = 16 * (lane >> 3);
+    const int ra = db + rho, rb = db + 14 - rho, split = 15 - rho;
+    if (!dwarp) {
+        int u = tid >> 4, ti = 0;
+        active = u < nt * (nt - 1) / 2;
+        if (active) {
+            while (u >= nt - 1 - ti) { u -= nt - 1 - ti; ++ti; }
+            qr = 16 * ti;
+            qc = 16 * (ti + 1 + u);
+        }
+    } else {
+        active = (lane >> 3) < nt;
+    }
+    const int dc = tid >> 1, dpart = tid & 1;   // diagonal sum share
+    const bool dact = dc < 16 * nt;
     for (int s = tid; s < KKMAX; s += nthr) cols[s] = s < kk ? slot[s] : -1;
     const unsigned long long signbit = 1ull << 63;
 
-    double t1[4][4], t2[4][4], t3[4][4];
+    double t1[16], t2[16], t3[16], dsum = 0.0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) { t1[i][j] = 0; t2[i][j] = 0; t3[i][j] = 0; }
+    for (int e = 0; e < 16; ++e) { t1[e] = 0; t2[e] = 0; t3[e] = 0; }
 
     for (int k0 = r0; k0 < r1; k0 += GRAM_KT) {
         __syncthreads();
@@ -81,55 +108,90 @@ __device__ __forceinline__ void gram_body_3m(const double2 *__restrict__ W, long
         }
         if (tid < GRAM_KT) sgn[tid] = (isH && Jrow[k0 + tid] < 0) ? signbit : 0ull;
         __syncthreads();
+        if (dact) {
+#pragma unroll 4
+            for (int k = 0; k < GRAM_KT; ++k) {
+                const double2 v = xs[k][dc];
+                const double c = dpart ? v.y : v.x;
+                dsum = fma(__longlong_as_double(__double_as_longlong(c) ^ sgn[k]), c, dsum);
+            }
+        }
         if (!active) continue;
+        if (!dwarp) {
 #pragma unroll 1
-        for (int k = 0; k < GRAM_KT; ++k) {
-            const unsigned long long sb = sgn[k];
-            double2 x[4], y[4];
-            double d[4], p[4];
+            for (int k = 0; k < GRAM_KT; ++k) {
+                const unsigned long long sb = sgn[k];
+                double2 x[4], y[4];
+                double d[4], p[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                x[i] = xs[k][qr + ly + 4 * i];
-                d[i] = xd[k][qr + ly + 4 * i];
-                x[i].x = __longlong_as_double(__double_as_longlong(x[i].x) ^ sb);
-                x[i].y = __longlong_as_double(__double_as_longlong(x[i].y) ^ sb);
-                d[i] = __longlong_as_double(__double_as_longlong(d[i]) ^ sb);
-            }
+                for (int i = 0; i < 4; ++i) {
+                    x[i] = xs[k][qr + ly + 4 * i];
+                    d[i] = xd[k][qr + ly + 4 * i];
+                    x[i].x = __longlong_as_double(__double_as_longlong(x[i].x) ^ sb);
+                    x[i].y = __longlong_as_double(__double_as_longlong(x[i].y) ^ sb);
+                    d[i] = __longlong_as_double(__double_as_longlong(d[i]) ^ sb);
+                }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                y[j] = xs[k][qc + lx + 4 * j];
-                p[j] = xp[k][qc + lx + 4 * j];
-            }
-            if (diag) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = i; j < 4; ++j) {
-                        t1[i][j] = fma(x[i].x, y[j].x, t1[i][j]);
-                        t2[i][j] = fma(x[i].y, y[j].y, t2[i][j]);
-                        t3[i][j] = fma(d[i], p[j], t3[i][j]);
-                    }
-            } else {
+                for (int j = 0; j < 4; ++j) {
+                    y[j] = xs[k][qc + lx + 4 * j];
+                    p[j] = xp[k][qc + lx + 4 * j];
+                }
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        t1[i][j] = fma(x[i].x, y[j].x, t1[i][j]);
-                        t2[i][j] = fma(x[i].y, y[j].y, t2[i][j]);
-                        t3[i][j] = fma(d[i], p[j], t3[i][j]);
+                        t1[4 * i + j] = fma(x[i].x, y[j].x, t1[4 * i + j]);
+                        t2[4 * i + j] = fma(x[i].y, y[j].y, t2[4 * i + j]);
+                        t3[4 * i + j] = fma(d[i], p[j], t3[4 * i + j]);
                     }
+            }
+        } else {
+#pragma unroll 1
+            for (int k = 0; k < GRAM_KT; ++k) {
+                const unsigned long long sb = sgn[k];
+                double2 xa = xs[k][ra], xb = xs[k][rb];
+                double da = xd[k][ra], dbv = xd[k][rb];
+                xa.x = __longlong_as_double(__double_as_longlong(xa.x) ^ sb);
+                xa.y = __longlong_as_double(__double_as_longlong(xa.y) ^ sb);
+                xb.x = __longlong_as_double(__double_as_longlong(xb.x) ^ sb);
+                xb.y = __longlong_as_double(__double_as_longlong(xb.y) ^ sb);
+                da = __longlong_as_double(__double_as_longlong(da) ^ sb);
+                dbv = __longlong_as_double(__double_as_longlong(dbv) ^ sb);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const bool a = e < split;
+                    const int c = db + (a ? rho + 1 + e : e);
+                    const double2 y = xs[k][c];
+                    const double p = xp[k][c];
+                    t1[e] = fma(a ? xa.x : xb.x, y.x, t1[e]);
+                    t2[e] = fma(a ? xa.y : xb.y, y.y, t2[e]);
+                    t3[e] = fma(a ? da : dbv, p, t3[e]);
+                }
             }
         }
     }
+    // the diagonal: both halves of column dc meet in lanes 2c, 2c + 1
+    dsum += __shfl_xor_sync(0xffffffffu, dsum, 1);
+    if (dact && dpart == 0) out[dc + KKMAX * dc] = make_double2(dsum, 0.0);
     if (!active) return;
+    if (!dwarp) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int ii = qr + ly + 4 * i, jj = qc + lx + 4 * j;
-            if (ii > jj) continue;
-            out[ii + KKMAX * jj] = make_double2(t1[i][j] + t2[i][j], (t3[i][j] - t1[i][j]) + t2[i][j]);
+            for (int j = 0; j < 4; ++j) {
+                const int e = 4 * i + j;
+                out[(qr + ly + 4 * i) + KKMAX * (qc + lx + 4 * j)] =
+                    make_double2(t1[e] + t2[e], (t3[e] - t1[e]) + t2[e]);
+            }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            if (rho == 7 && e >= 8) continue;      // row 7 has 8 entries
+            const bool a = e < split;
+            const int r = a ? ra : rb, c = db + (a ? rho + 1 + e : e);
+            out[r + KKMAX * c] = make_double2(t1[e] + t2[e], (t3[e] - t1[e]) + t2[e]);
         }
+    }
 }
 
 // The body, for one (pair, row chunk): rows [r0, r1) of W (ld), the pair's
@@ -246,7 +308,7 @@ __device__ __forceinline__ void gram_body(const typename cplx<T>::t *__restrict_
 
 // One outer step of one pencil: CTA = (pair, row chunk).
 template <typename T>
-__global__ void __launch_bounds__(160, sizeof(T) == 8 ? 2 : 3)
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 128 : 160, 3)
 gram_kernel(const typename cplx<T>::t *__restrict__ W, const int8_t *__restrict__ Jrow,
             StepArgs a, typename cplx<T>::t *__restrict__ partial)
 {

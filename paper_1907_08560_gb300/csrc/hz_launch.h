@@ -43,12 +43,20 @@ struct InnerArgs {
     int param32;                       // complex64 sweeps: 2x2 parameters in FP32
 };
 
-// Threads of a Gram CTA: 16 per upper-triangular 16 x 16 tile of the kk x kk pivot.
+// Threads of a complex64 Gram CTA: 16 per upper-triangular 16 x 16 tile of the kk x kk pivot.
 inline int gram_threads(int kk)
 {
     const int nt = (kk + 15) / 16;
     const int t = 16 * nt * (nt + 1) / 2;
     return t < 32 ? 32 : t;
+}
+
+// Threads of a complex128 Gram CTA: whole warps for the off-diagonal tiles
+// (16 threads each) and one warp for the diagonal tiles; 128 at kk = 64.
+inline int gram_threads_c128(int kk)
+{
+    const int nt = (kk + 15) / 16;
+    return 32 * ((8 * nt * (nt - 1) + 31) / 32 + 1);
 }
 
 // Error flags raised by the device (bitwise or).

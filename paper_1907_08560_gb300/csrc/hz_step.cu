@@ -493,7 +493,7 @@ cudaError_t launch_gram(const void *W, bool single, const int8_t *Jrow, const St
                         void *partial, cudaStream_t s)
 {
     const int grid = a.npairs * (a.chunks_h + a.chunks_s);
-    const int threads = gram_threads(a.kk);
+    const int threads = single ? gram_threads(a.kk) : gram_threads_c128(a.kk);
     if (single)
         gram_kernel<float><<<grid, threads, 0, s>>>((const float2 *)W, Jrow, a, (float2 *)partial);
     else
