@@ -143,25 +143,11 @@ static int partition(int n, int w, std::vector<int> &off)
     return nb;
 }
 
-// Gram chunk: the multiple of GRAM_KT rows that balances the per-step Gram
-// CTAs over the SMs best (ties: the larger chunk, fewer partials to sum).
+// Gram chunk: forced by the options, else the balance rule of gram_chunk_rows.
 static int choose_chunk(int m_pad, int p_pad, int npairs, int sms, int forced)
 {
     if (forced > 0) return (int)round_up(forced, hz::GRAM_KT);
-    long long best_cost = -1;
-    int best = 512;
-    for (int kc = 128; kc <= 4096; kc += 64) {
-        const long long ch = (m_pad + kc - 1) / kc + (p_pad + kc - 1) / kc;
-        const long long ctas = ch * npairs;
-        const long long waves = (ctas + sms - 1) / sms;
-        // time ~ waves * kc + partial-sum work in the inner kernel
-        const long long cost = waves * kc + ch * 8;
-        if (best_cost < 0 || cost < best_cost || (cost == best_cost && kc > best)) {
-            best_cost = cost;
-            best = kc;
-        }
-    }
-    return best;
+    return hz::gram_chunk_rows(m_pad, p_pad, npairs, sms);
 }
 
 static bool is_device_ptr(const void *p)
@@ -448,6 +434,10 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
         // new complex64 round starts from fl32 of the improved W, whose columns
         // are now nearly orthogonal so that rounding them to complex64 no
         // longer perturbs the ill-conditioned directions.  FP64 sweeps finish.
+        // Two rounds: a third and fourth (n = 2048 pencil: 7 more complex64
+        // sweeps and two more FP64 products) spared one nearly empty FP64
+        // sweep and took 0.5 s more than they saved.
+        constexpr int kMaxRounds = 2;
         int phase_single = mixed ? 1 : 0;
         int round_sweeps = 0;
         unsigned long long prev_big = ~0ULL;
@@ -528,7 +518,7 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
                                              cudaMemcpyDeviceToDevice, st));
                     h->stats.kernel_launches += 1;
                     ++rounds;
-                    if (budget || all == 0 || round_sweeps <= 3 || rounds >= 4) {
+                    if (budget || all == 0 || round_sweeps <= 3 || rounds >= kMaxRounds) {
                         phase_single = 0;            // FP64 finishing sweeps
                     } else {                         // next complex64 round
                         CUDA_TRY(hz::launch_convert(h->W32, true, h->W, Mt * n, st));

@@ -139,16 +139,7 @@ extern "C" ghsvd_status ghsvd_solve_noalloc(int64_t m64, int64_t p64, int64_t n6
     if (o.gram_chunk > 0) {
         kc = (o.gram_chunk + hz::GRAM_KT - 1) / hz::GRAM_KT * hz::GRAM_KT;
     } else {
-        long long best_cost = -1;
-        for (int c = 128; c <= 4096; c += 64) {
-            const long long ch = (m_pad + c - 1) / c + (p_pad + c - 1) / c;
-            const long long waves = (ch * npairs + sms - 1) / sms;
-            const long long cost = waves * c + ch * 8;
-            if (best_cost < 0 || cost < best_cost || (cost == best_cost && c > kc)) {
-                best_cost = cost;
-                kc = c;
-            }
-        }
+        kc = hz::gram_chunk_rows(m_pad, p_pad, npairs, sms);
     }
     const int chunks_h = (m_pad + kc - 1) / kc, chunks_s = (p_pad + kc - 1) / kc;
     const int cpp = chunks_h + chunks_s;

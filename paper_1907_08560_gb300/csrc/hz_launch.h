@@ -59,6 +59,33 @@ inline int gram_threads_c128(int kk)
     return 32 * ((8 * nt * (nt - 1) + 31) / 32 + 1);
 }
 
+// Gram row chunk (a multiple of GRAM_KT): the chunk whose per-step CTAs
+// (npairs x chunks) spread over the SMs best, time ~ waves x rows per chunk
+// plus the partial sums the inner level reads; ties go to the larger chunk.
+// Only chunks giving at least two CTAs per SM compete when any does: with one
+// CTA per SM the loads of a staged row block are not hidden behind another
+// CTA's FMAs and SMs idle (the 2048 + 2048 rows of a shortened pencil: 1024-row
+// chunks, 128 CTAs, Gram 2.46 ms per step; 320-row chunks, 448 CTAs, 1.61 ms).
+inline int gram_chunk_rows(int m_pad, int p_pad, int npairs, int sms)
+{
+    long long best_cost = -1;
+    int best = 512;
+    for (int pass = 0; pass < 2 && best_cost < 0; ++pass) {
+        for (int kc = 128; kc <= 4096; kc += 64) {
+            const long long ch = (m_pad + kc - 1) / kc + (p_pad + kc - 1) / kc;
+            const long long ctas = ch * npairs;
+            if (pass == 0 && ctas < 2LL * sms) continue;
+            const long long waves = (ctas + sms - 1) / sms;
+            const long long cost = waves * kc + ch * 8;
+            if (best_cost < 0 || cost < best_cost || (cost == best_cost && kc > best)) {
+                best_cost = cost;
+                best = kc;
+            }
+        }
+    }
+    return best;
+}
+
 // Error flags raised by the device (bitwise or).
 constexpr int DEVERR_RANK = 1;
 constexpr int DEVERR_NONFINITE = 2;
