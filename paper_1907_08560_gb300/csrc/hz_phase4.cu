@@ -45,6 +45,11 @@ __device__ __forceinline__ void better(double &v, long long &i, double v2, long 
     if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
 }
 
+// The last stage runs in warp 0 and is broadcast through shared memory (a
+// warp's FP64 instruction holds its sub-partition's FP64 pipe for 64 cycles,
+// so every thread repeating it costs NT/32 times as much); better is a total
+// order on the values that can win (NaN never does), so the tree picks what a
+// scan in warp order would.
 template <int NT>
 __device__ void block_argmax(double &v, long long &i, double *shv, long long *shi)
 {
@@ -57,9 +62,20 @@ __device__ void block_argmax(double &v, long long &i, double *shv, long long *sh
     __syncthreads();
     if (l == 0) { shv[w] = v; shi[w] = i; }
     __syncthreads();
+    if (w == 0) {
+        v = l < NT / 32 ? shv[l] : shv[0];
+        i = l < NT / 32 ? shi[l] : shi[0];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            const long long i2 = __shfl_xor_sync(0xffffffffu, i, o);
+            better(v, i, v2, i2);
+        }
+        __syncwarp();
+        if (l == 0) { shv[0] = v; shi[0] = i; }
+    }
+    __syncthreads();
     v = shv[0];
     i = shi[0];
-    for (int k = 1; k < NT / 32; ++k) better(v, i, shv[k], shi[k]);
     __syncthreads();
 }
 

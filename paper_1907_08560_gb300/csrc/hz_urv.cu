@@ -57,16 +57,26 @@ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_dou
 __device__ __forceinline__ double abs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
 // ---- block reductions (fixed order: deterministic) -------------------------
+// Block reductions.  The last stage runs in one thread (sum, in warp order)
+// or one warp (argmax) and is broadcast through shared memory: on GB300 a
+// warp's FP64 instruction holds its sub-partition's FP64 pipe for 64 cycles,
+// so NT threads each repeating the last stage cost NT/32 times as much.
 template <int NT>
 __device__ double block_sum(double v, double *sh)
 {
+    __shared__ double s_sum;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
     if (l == 0) sh[w] = v;
     __syncthreads();
-    double r = 0.0;
-    for (int i = 0; i < NT / 32; ++i) r += sh[i];
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int i = 0; i < NT / 32; ++i) r += sh[i];
+        s_sum = r;
+    }
+    __syncthreads();
+    const double r = s_sum;
     __syncthreads();
     return r;
 }
@@ -85,6 +95,8 @@ __device__ __forceinline__ void better(double &v, int &i, double v2, int i2)
     if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
 }
 
+// (better is a total order on the values that can win -- NaN never does --
+// so the tree in warp 0 picks what a scan in warp order would.)
 template <int NT>
 __device__ void block_argmax(double &v, int &i, double *shv, int *shi)
 {
@@ -97,9 +109,20 @@ __device__ void block_argmax(double &v, int &i, double *shv, int *shi)
     __syncthreads();
     if (l == 0) { shv[w] = v; shi[w] = i; }
     __syncthreads();
+    if (w == 0) {
+        v = l < NT / 32 ? shv[l] : shv[0];
+        i = l < NT / 32 ? shi[l] : shi[0];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+            better(v, i, v2, i2);
+        }
+        __syncwarp();
+        if (l == 0) { shv[0] = v; shi[0] = i; }
+    }
+    __syncthreads();
     v = shv[0];
     i = shi[0];
-    for (int k = 1; k < NT / 32; ++k) better(v, i, shv[k], shi[k]);
     __syncthreads();
 }
 
