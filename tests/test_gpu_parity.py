@@ -65,12 +65,23 @@ def test_single_pencil_64_eigenvalues_match_oracle(gh, w):
     check_eigs(F, G, J, gpu, ref_pw)
 
 
-def test_one_sweep_factors_match_oracle_elementwise(gh):
+def _pencil(case):
+    if case == "single64":
+        return P.single_pencil_64()
+    n = int(case[1:])
+    return P.svd_pencil(900 + n, (3 * n) // 2 + 3, 2 * n + 5, n, n // 5, (1e-2, 1e2), (1e-3, 1e3),
+                        permute_j=True)
+
+
+# block pivots of 16 (one 16 x 16 tile of the Gram), 48 and 34 columns (three
+# tiles, the last one ragged at 34) and 64 (four tiles)
+@pytest.mark.parametrize("case,w", [("single64", 8), ("n96", 24), ("n100", 20), ("n128", 32)])
+def test_one_sweep_factors_match_oracle_elementwise(gh, case, w):
     # the same block algorithm, same orderings: after one sweep the
     # transformed factors agree to rounding (relative to each column's norm)
-    F, J, G = P.single_pencil_64()
-    ref = oracle.blocked(F, G, J, w=8, max_sweeps=1)
-    gpu = gpu_solve(gh, F, G, J, block_width=8, max_sweeps=1)
+    F, J, G = _pencil(case)
+    ref = oracle.blocked(F, G, J, w=w, max_sweeps=1)
+    gpu = gpu_solve(gh, F, G, J, block_width=w, max_sweeps=1)
     assert gpu["status"] == gh.GHSVD_ERR_NOT_CONVERGED
     assert gpu["stats"]["transforms"][0] == ref["counts"][0, 0]
     for X in ("F", "G", "Z"):
@@ -81,7 +92,8 @@ def test_one_sweep_factors_match_oracle_elementwise(gh):
 
 
 @pytest.mark.parametrize("m,p,n,neg,w", [(70, 90, 65, 20, 8), (40, 41, 37, 10, 5),
-                                         (130, 200, 100, 40, 7), (9, 8, 7, 3, 2)])
+                                         (130, 200, 100, 40, 7), (9, 8, 7, 3, 2),
+                                         (150, 200, 96, 30, 24), (170, 230, 100, 33, 20)])
 def test_ragged_and_odd_sizes(gh, m, p, n, neg, w):
     # odd n (bordering), uneven block widths, row counts not multiples of 64
     F, J, G = P.svd_pencil(500 + n, m, p, n, neg, (1e-2, 1e2), (1e-2, 1e2), permute_j=True)
