@@ -14,4 +14,17 @@ template <typename T> struct cplx;
 template <> struct cplx<double> { using t = double2; };
 template <> struct cplx<float> { using t = float2; };
 
+// Asynchronous copy of one B-byte element (B = 4, 8 or 16) from global to
+// shared memory through L1 (cp.async), the commit of the copies issued so far
+// as a group, and the wait until at most N groups are still in flight.
+template <int B>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 }  // namespace hz

@@ -196,7 +196,10 @@ __device__ __forceinline__ void gram_body_3m(const double2 *__restrict__ W, long
 
 // The body, for one (pair, row chunk): rows [r0, r1) of W (ld), the pair's
 // kk slot columns `slot`, J signs applied iff isH; writes the partial to out.
-// The complex64 form uses four real FMA chains per entry.
+// The complex64 form uses four real FMA chains per entry, and stages the row
+// blocks in two shared buffers: the cp.async copies of block b + 1 are in
+// flight while block b is multiplied (the FP32 pipe does not hide a load
+// round trip per block by itself).
 template <typename T>
 __device__ __forceinline__ void gram_body_4m(const typename cplx<T>::t *__restrict__ W, long long ld,
                                           const int8_t *__restrict__ Jrow,
@@ -205,8 +208,8 @@ __device__ __forceinline__ void gram_body_4m(const typename cplx<T>::t *__restri
 {
     using T2 = typename cplx<T>::t;
     using U = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
-    __shared__ T2 xs[GRAM_KT][KKMAX + 1];   // padded: the staging stores walk down rows
-    __shared__ U sgn[GRAM_KT];
+    __shared__ T2 xs[2][GRAM_KT][KKMAX + 1];   // padded: the staging stores walk down rows
+    __shared__ U sgn[2][GRAM_KT];
     __shared__ int cols[KKMAX];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lx = tid & 3, ly = (tid >> 2) & 3;
@@ -223,61 +226,83 @@ __device__ __forceinline__ void gram_body_4m(const typename cplx<T>::t *__restri
 #pragma unroll
         for (int j = 0; j < 4; ++j) { accr[i][j] = 0; acci[i][j] = 0; }
 
-    for (int k0 = r0; k0 < r1; k0 += GRAM_KT) {
-        __syncthreads();
-        // stage GRAM_KT rows x KKMAX slots; consecutive threads read consecutive rows
+    // stage GRAM_KT rows x KKMAX slots of block k0 into buffer b;
+    // consecutive threads copy consecutive rows
+    auto stage = [&](int b, int k0) {
         for (int e = tid; e < GRAM_KT * KKMAX; e += nthr) {
             const int r = e % GRAM_KT, s = e / GRAM_KT;
             const int col = cols[s];
-            T2 v;
-            if (col >= 0) v = W[(long long)col * ld + k0 + r];
-            else { v.x = 0; v.y = 0; }
-            xs[r][s] = v;
+            if (col >= 0) {
+                cp_async<sizeof(T2)>(&xs[b][r][s], W + (long long)col * ld + k0 + r);
+            } else {
+                T2 z;
+                z.x = 0;
+                z.y = 0;
+                xs[b][r][s] = z;
+            }
         }
-        if (tid < GRAM_KT) sgn[tid] = (isH && Jrow[k0 + tid] < 0) ? signbit : (U)0;
+        cp_async_commit();
+    };
+    __syncthreads();                               // cols
+    stage(0, r0);
+    if (tid < GRAM_KT) sgn[0][tid] = (isH && Jrow[r0 + tid] < 0) ? signbit : (U)0;
+    int b = 0;
+    for (int k0 = r0; k0 < r1; k0 += GRAM_KT, b ^= 1) {
+        const bool more = k0 + GRAM_KT < r1;
+        int8_t jnext = 1;                          // sign of row tid of the next block
+        if (more) {
+            stage(b ^ 1, k0 + GRAM_KT);
+            if (isH && tid < GRAM_KT) jnext = Jrow[k0 + GRAM_KT + tid];
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         __syncthreads();
-        if (!active) continue;
+        if (active) {
 #pragma unroll 4
-        for (int k = 0; k < GRAM_KT; ++k) {
-            const U sb = sgn[k];
-            T2 x[4], y[4];
+            for (int k = 0; k < GRAM_KT; ++k) {
+                const U sb = sgn[b][k];
+                T2 x[4], y[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                x[i] = xs[k][qr + ly + 4 * i];
-                if (sizeof(T) == 8) {
-                    x[i].x = __longlong_as_double(__double_as_longlong(x[i].x) ^ sb);
-                    x[i].y = __longlong_as_double(__double_as_longlong(x[i].y) ^ sb);
+                for (int i = 0; i < 4; ++i) {
+                    x[i] = xs[b][k][qr + ly + 4 * i];
+                    if (sizeof(T) == 8) {
+                        x[i].x = __longlong_as_double(__double_as_longlong(x[i].x) ^ sb);
+                        x[i].y = __longlong_as_double(__double_as_longlong(x[i].y) ^ sb);
+                    } else {
+                        x[i].x = __int_as_float(__float_as_int(x[i].x) ^ (unsigned)sb);
+                        x[i].y = __int_as_float(__float_as_int(x[i].y) ^ (unsigned)sb);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) y[j] = xs[b][k][qc + lx + 4 * j];
+                // acc_ij += conj(J x_i) y_j; in a diagonal tile the entries below
+                // the diagonal (i > j) are not needed (the block pivot is Hermitian)
+                if (diag) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = i; j < 4; ++j) {
+                            accr[i][j] = fma(x[i].x, y[j].x, accr[i][j]);
+                            accr[i][j] = fma(x[i].y, y[j].y, accr[i][j]);
+                            acci[i][j] = fma(x[i].x, y[j].y, acci[i][j]);
+                            acci[i][j] = fma(-x[i].y, y[j].x, acci[i][j]);
+                        }
                 } else {
-                    x[i].x = __int_as_float(__float_as_int(x[i].x) ^ (unsigned)sb);
-                    x[i].y = __int_as_float(__float_as_int(x[i].y) ^ (unsigned)sb);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            accr[i][j] = fma(x[i].x, y[j].x, accr[i][j]);
+                            accr[i][j] = fma(x[i].y, y[j].y, accr[i][j]);
+                            acci[i][j] = fma(x[i].x, y[j].y, acci[i][j]);
+                            acci[i][j] = fma(-x[i].y, y[j].x, acci[i][j]);
+                        }
                 }
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) y[j] = xs[k][qc + lx + 4 * j];
-            // acc_ij += conj(J x_i) y_j; in a diagonal tile the entries below
-            // the diagonal (i > j) are not needed (the block pivot is Hermitian)
-            if (diag) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = i; j < 4; ++j) {
-                        accr[i][j] = fma(x[i].x, y[j].x, accr[i][j]);
-                        accr[i][j] = fma(x[i].y, y[j].y, accr[i][j]);
-                        acci[i][j] = fma(x[i].x, y[j].y, acci[i][j]);
-                        acci[i][j] = fma(-x[i].y, y[j].x, acci[i][j]);
-                    }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        accr[i][j] = fma(x[i].x, y[j].x, accr[i][j]);
-                        accr[i][j] = fma(x[i].y, y[j].y, accr[i][j]);
-                        acci[i][j] = fma(x[i].x, y[j].y, acci[i][j]);
-                        acci[i][j] = fma(-x[i].y, y[j].x, acci[i][j]);
-                    }
-            }
         }
+        if (more && tid < GRAM_KT) sgn[b ^ 1][tid] = jnext < 0 ? signbit : (U)0;
+        __syncthreads();                           // buffer b is free for block k0 + 2 GRAM_KT
     }
     // out[i + KKMAX j] (column-major), entries on and above the diagonal only
     if (!active) return;

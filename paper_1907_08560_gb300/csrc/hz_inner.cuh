@@ -88,11 +88,13 @@ __device__ __forceinline__ void c_left(T2 &x0, T2 &x1, const T *z)
 // One CTA (1024 threads) per block pivot; H^, S^, Z^ live in shared memory.
 // ---------------------------------------------------------------------------
 // The body, for one block pivot: pp = its cpp Gram partials, slot = its kk
-// slot columns, zo = its Z^ (FP64, ld KKMAX), flag = its "transformed" flag.
+// slot columns, zo = its Z^ (in the sweep's precision TU, ld KKMAX), flag =
+// its "transformed" flag.
 template <typename TP, typename TU, int CL = 1>
 __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restrict__ pp,
                                            const int *__restrict__ slot, InnerArgs a,
-                                           double2 *__restrict__ zo, int *__restrict__ flag,
+                                           typename cplx<TU>::t *__restrict__ zo,
+                                           int *__restrict__ flag,
                                            unsigned long long *__restrict__ counters,
                                            int *__restrict__ err, unsigned char *smraw_inner)
 {
@@ -285,7 +287,7 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
     for (int idx = tid * CL + crank; idx < kk * kk; idx += CL * blockDim.x) {
         const int i = idx % kk, j = idx / kk;
         const U2 v = Z[i + INNER_LD * j];
-        zo[i + KKMAX * j] = make_double2((double)v.x, (double)v.y);
+        zo[i + KKMAX * j] = v;
     }
     if (tid == 0 && crank == 0) {
         *flag = s_all > 0;
@@ -299,7 +301,7 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
 template <typename TP, typename TU>
 __global__ void __launch_bounds__(1024)
 inner_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__restrict__ slotcol,
-             InnerArgs a, double2 *__restrict__ zhat, int *__restrict__ pair_flag,
+             InnerArgs a, typename cplx<TU>::t *__restrict__ zhat, int *__restrict__ pair_flag,
              unsigned long long *__restrict__ counters, int *__restrict__ err)
 {
     extern __shared__ unsigned char smraw_inner[];
@@ -313,7 +315,7 @@ inner_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__rest
 template <typename TP, typename TU, int CL>
 __global__ void __launch_bounds__(1024)
 inner_cluster_kernel(const typename cplx<TP>::t *__restrict__ partial, const int *__restrict__ slotcol,
-                     InnerArgs a, double2 *__restrict__ zhat, int *__restrict__ pair_flag,
+                     InnerArgs a, typename cplx<TU>::t *__restrict__ zhat, int *__restrict__ pair_flag,
                      unsigned long long *__restrict__ counters, int *__restrict__ err)
 {
     extern __shared__ unsigned char smraw_inner[];

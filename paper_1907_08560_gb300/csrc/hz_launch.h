@@ -121,6 +121,8 @@ cudaError_t launch_signs(int8_t *Jrow, const int8_t *J, int m, int m_pad, long l
 cudaError_t launch_convert(void *dst, bool dst_single, const void *src, long long count, cudaStream_t s);
 cudaError_t launch_gram(const void *W, bool single, const int8_t *Jrow, const StepArgs &a,
                         void *partial, cudaStream_t s);
+// zhat: npairs x KKMAX^2 transformations Z^, complex128 for the FP64 sweeps and
+// complex64 (in the same storage) for the complex64 sweeps (single).
 cudaError_t launch_inner(const void *partial, bool single, const int *slotcol, const InnerArgs &a,
                          double2 *zhat, int *pair_flag, unsigned long long *counters, int *err,
                          cudaStream_t s);

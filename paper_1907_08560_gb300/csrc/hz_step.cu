@@ -547,7 +547,7 @@ cudaError_t setup_kernels()
     e = cudaFuncSetAttribute(update_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)update_smem(sizeof(double2)));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(update_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(update_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)update_smem(sizeof(float2)));
     if (e != cudaSuccess) return e;
     if (g_cluster_mask < 0) {
@@ -582,8 +582,8 @@ static cudaError_t launch_inner_cluster(const void *partial, const int *slotcol,
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, inner_cluster_kernel<TP, TU, CL>,
-                              (const typename cplx<TP>::t *)partial, slotcol, a, zhat, pair_flag,
-                              counters, err);
+                              (const typename cplx<TP>::t *)partial, slotcol, a,
+                              (typename cplx<TU>::t *)zhat, pair_flag, counters, err);
 }
 
 cudaError_t launch_inner(const void *partial, bool single, const int *slotcol, const InnerArgs &a,
@@ -612,7 +612,7 @@ cudaError_t launch_inner(const void *partial, bool single, const int *slotcol, c
     }
     if (single)
         inner_kernel<float, float><<<a.npairs, 1024, inner_smem(true), s>>>(
-            (const float2 *)partial, slotcol, a, zhat, pair_flag, counters, err);
+            (const float2 *)partial, slotcol, a, (float2 *)zhat, pair_flag, counters, err);
     else
         inner_kernel<double, double><<<a.npairs, 1024, inner_smem(false), s>>>(
             (const double2 *)partial, slotcol, a, zhat, pair_flag, counters, err);
@@ -624,9 +624,9 @@ cudaError_t launch_update(void *W, bool single, const StepArgs &a, const double2
 {
     const long long Mt = (long long)a.m_pad + a.p_pad + a.n_pad;
     dim3 grid((unsigned)(Mt / UPD_R), a.npairs);
-    if (single)
-        update_kernel<float, double><<<grid, 256, update_smem(sizeof(float2)), s>>>(
-            (float2 *)W, a, zhat, pair_flag);
+    if (single)     // complex64 sweeps: Z^ is complex64 (the inner level's own precision)
+        update_kernel<float, float><<<grid, 256, update_smem(sizeof(float2)), s>>>(
+            (float2 *)W, a, (const float2 *)zhat, pair_flag);
     else
         update_kernel<double, double><<<grid, 256, update_smem(sizeof(double2)), s>>>(
             (double2 *)W, a, zhat, pair_flag);

@@ -28,14 +28,33 @@ __device__ __forceinline__ void update_body_3m(double2 *__restrict__ W, long lon
     __shared__ int ident[KKMAX];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     if (tid < KKMAX) cols[tid] = tid < kk ? slot[tid] : -1;
+    // Z^ (column-major in zp) and the row tile by asynchronous copies, all in
+    // flight at once; then the real sums from shared memory
     for (int idx = tid; idx < KKMAX * KKMAX; idx += 256) {
-        const int l = idx % KKMAX, j = idx / KKMAX;   // zhat column-major
-        double2 v = make_double2(0.0, 0.0);
-        if (l < kk && j < kk) v = zp[l + KKMAX * j];
-        zs[l * UPD_LD + j] = v;
+        const int l = idx % KKMAX, j = idx / KKMAX;
+        if (l < kk && j < kk) cp_async<16>(&zs[l * UPD_LD + j], &zp[l + KKMAX * j]);
+        else zs[l * UPD_LD + j] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();                               // cols
+    for (int idx = tid; idx < UPD_R * KKMAX; idx += 256) {
+        const int r = idx % UPD_R, s = idx / UPD_R;
+        const int col = cols[s];
+        if (col >= 0) cp_async<16>(&xs[r * UPD_LD + s], &W[(long long)col * ld + row0 + r]);
+        else xs[r * UPD_LD + s] = make_double2(0.0, 0.0);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    for (int idx = tid; idx < KKMAX * KKMAX; idx += 256) {
+        const int l = idx % KKMAX, j = idx / KKMAX;
+        const double2 v = zs[l * UPD_LD + j];
         zsum[l * UPD_LD + j] = v.x + v.y;
     }
-    __syncthreads();
+    for (int idx = tid; idx < UPD_R * KKMAX; idx += 256) {
+        const int r = idx % UPD_R, s = idx / UPD_R;
+        const double2 v = xs[r * UPD_LD + s];
+        xsum[r * UPD_LD + s] = v.x + v.y;
+    }
     if (tid < KKMAX) {
         int id = 1;
         for (int l = 0; l < KKMAX; ++l) {
@@ -43,14 +62,6 @@ __device__ __forceinline__ void update_body_3m(double2 *__restrict__ W, long lon
             id &= (v.x == (l == tid ? 1.0 : 0.0)) & (v.y == 0.0);
         }
         ident[tid] = id;
-    }
-    for (int idx = tid; idx < UPD_R * KKMAX; idx += 256) {
-        const int r = idx % UPD_R, s = idx / UPD_R;
-        const int col = cols[s];
-        double2 v = make_double2(0.0, 0.0);
-        if (col >= 0) v = W[(long long)col * ld + row0 + r];
-        xs[r * UPD_LD + s] = v;
-        xsum[r * UPD_LD + s] = v.x + v.y;
     }
     __syncthreads();
     double t1[4][4], t2[4][4], t3[4][4];
@@ -115,25 +126,29 @@ __device__ __forceinline__ void update_body_4m(typename cplx<T>::t *__restrict__
     // (consecutive threads on consecutive rows) then hit distinct banks
     T2 *zs = reinterpret_cast<T2 *>(smraw);          // [KKMAX][UPD_LD] row l, col j
     T2 *xs = zs + KKMAX * UPD_LD;                     // [UPD_R][UPD_LD]
+    static_assert(std::is_same<T, TZ>::value, "Z^ in the sweep's precision");
     __shared__ int cols[KKMAX];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     if (tid < KKMAX) cols[tid] = tid < kk ? slot[tid] : -1;
+    // Z^ (column-major in zp) and the row tile by asynchronous copies, all in
+    // flight at once
+    T2 zero;
+    zero.x = 0;
+    zero.y = 0;
     for (int idx = tid; idx < KKMAX * KKMAX; idx += 256) {
-        const int l = idx % KKMAX, j = idx / KKMAX;   // zhat column-major
-        T2 v;
-        if (l < kk && j < kk) { v.x = (T)zp[l + KKMAX * j].x; v.y = (T)zp[l + KKMAX * j].y; }
-        else { v.x = 0; v.y = 0; }
-        zs[l * UPD_LD + j] = v;
+        const int l = idx % KKMAX, j = idx / KKMAX;
+        if (l < kk && j < kk) cp_async<sizeof(T2)>(&zs[l * UPD_LD + j], &zp[l + KKMAX * j]);
+        else zs[l * UPD_LD + j] = zero;
     }
-    __syncthreads();
+    __syncthreads();                               // cols
     for (int idx = tid; idx < UPD_R * KKMAX; idx += 256) {
         const int r = idx % UPD_R, s = idx / UPD_R;
         const int col = cols[s];
-        T2 v;
-        if (col >= 0) v = W[(long long)col * ld + row0 + r];
-        else { v.x = 0; v.y = 0; }
-        xs[r * UPD_LD + s] = v;
+        if (col >= 0) cp_async<sizeof(T2)>(&xs[r * UPD_LD + s], &W[(long long)col * ld + row0 + r]);
+        else xs[r * UPD_LD + s] = zero;
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     T accr[4][4], acci[4][4];
 #pragma unroll
