@@ -11,11 +11,13 @@ namespace hz {
 // the inner kernel sums the partials in a fixed order.
 //
 // The block pivots are Hermitian, so only the entries on and above the
-// diagonal are computed: the 16 x 16 tiles on and above the diagonal (10 of 16
-// for kk = 64, 3 of 4 for kk = 32), 16 threads per tile, each a 4 x 4 set of
-// complex outputs (rows 16 ti + ly + 4i, columns 16 tj + lx + 4j); in the
-// diagonal tiles the 4 x 4 blocks below the diagonal are skipped.  J enters as a sign flip of the conjugated factor
-// (an integer xor on the sign bits).
+// diagonal are computed.  The complex64 body takes the 16 x 16 tiles on and
+// above the diagonal (10 of 16 for kk = 64, 3 of 4 for kk = 32), 16 threads
+// per tile, each a 4 x 4 set of complex outputs (rows 16 ti + ly + 4i,
+// columns 16 tj + lx + 4j), skipping in the diagonal tiles the 4 x 4 blocks
+// below the diagonal; the complex128 body deals the same entries out in equal
+// FP64 shares per warp (below).  J enters as a sign flip of the conjugated
+// factor (an integer xor on the sign bits).
 // ---------------------------------------------------------------------------
 // The tile of one thread: the nt diagonal tiles first (so that warps hold two
 // diagonal tiles or two off-diagonal ones), then the tiles above the diagonal
