@@ -86,7 +86,11 @@ typedef struct {
     int crit_mode;       /* eq. 6.12 reading: 0 = |h_pq| >= sqrt(max) eps
                             sqrt(n) sqrt(min) (default), 1 = as printed       */
     int precision;       /* GHSVD_PRECISION_FP64 (default) or _MIXED           */
-    int mixed_max_sweeps;/* at most this many complex64 sweeps (default 24)    */
+    int mixed_max_sweeps;/* at most this many complex64 sweeps (default 24);
+                            they count toward max_sweeps.  The two rounds end
+                            where their big count levels off: 36 + 12 sweeps
+                            for the n = 2048 benchmark pencil, which is solved
+                            with 60 and max_sweeps 80                         */
     int sort_ascending;  /* 1: sort lambda ascending and permute V alike;
                             0 (default): column order of the iteration, as in
                             the paper (Section 3)                              */
