@@ -54,6 +54,34 @@ def test_pivot_diagonalizes_random_pairs():
         check_diagonalizes(H, S, Z)
 
 
+def test_pivot_invariants_over_1e5_random_pivots():
+    # eq. 6.1-6.11 on 10^5 pivots of random factors (signatures with 0-3
+    # negative rows, column scales over six decades): Z'^* S Z' = I and
+    # Z'^* H Z' diagonal relative to its diagonal, checked all at once
+    rng = np.random.default_rng(7)
+    N = 100_000
+    A = rng.standard_normal((N, 6, 2)) + 1j * rng.standard_normal((N, 6, 2))
+    B = rng.standard_normal((N, 7, 2)) + 1j * rng.standard_normal((N, 7, 2))
+    A[:, :, 1] *= (10.0 ** rng.uniform(-3, 3, N))[:, None]
+    B[:, :, 1] *= (10.0 ** rng.uniform(-3, 3, N))[:, None]
+    J = np.ones((N, 6))
+    J[np.arange(6)[None, :] < rng.integers(0, 4, N)[:, None]] = -1.0
+    H = np.einsum("nri,nr,nrj->nij", A.conj(), J, A)
+    S = np.einsum("nri,nrj->nij", B.conj(), B)
+    lib = oracle.load()
+    Z = np.empty((N, 2, 2), dtype=np.complex128)
+    for t in range(N):
+        rc, Z[t], big = oracle.pivot(H[t, 0, 0].real, H[t, 1, 1].real, H[t, 0, 1], S[t, 0, 0].real,
+                                     S[t, 1, 1].real, S[t, 0, 1], lib=lib)
+        assert rc == 1 and big == 1, t
+    S3 = np.einsum("nki,nkl,nlj->nij", Z.conj(), S, Z)
+    H3 = np.einsum("nki,nkl,nlj->nij", Z.conj(), H, Z)
+    assert np.max(np.abs(S3 - np.eye(2)[None])) <= 2e-13
+    scale = np.maximum(np.sqrt(np.abs(H3[:, 0, 0].real * H3[:, 1, 1].real)) + 1e-3 * np.abs(H3).max(axis=(1, 2)),
+                       np.abs(H3).max(axis=(1, 2)))
+    assert np.all(np.abs(H3[:, 0, 1]) <= 1e-12 * scale)
+
+
 def test_pivot_exceptional_case_already_diagonal():
     # Section 6.1.6: h_pq = s_pq = 0 gives no transformation
     rc, Z, big = oracle.pivot(2.0, -3.0, 0.0, 4.0, 5.0, 0.0)
