@@ -20,6 +20,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <chrono>
 #include <mutex>
 
 #include "../../include/ghsvd.h"
@@ -86,25 +87,32 @@ extern "C" ghsvd_status ghsvd_solve_noalloc(int64_t m64, int64_t p64, int64_t n6
                                             int64_t ldv, const ghsvd_opts *opts, int *sweeps_out,
                                             void *stream)
 {
+    auto t0 = std::chrono::steady_clock::now();
+    if (sweeps_out) *sweeps_out = 0;             // written on every return
     ghsvd_opts o;
     if (opts) o = *opts;
     else ghsvd_default_opts(&o);
+    if (o.block_width == 0) o.block_width = 32;  // automatic: 32 for one pencil
     if (!F || !G || !lambda) return GHSVD_ERR_INVALID_ARG;
     if (n64 < 1 || m64 < n64 || p64 < n64 || ldf < m64 || ldg < p64 || (V && ldv < n64))
         return GHSVD_ERR_INVALID_ARG;
     if (!J && (n_plus < 0 || n_plus > m64)) return GHSVD_ERR_INVALID_ARG;
     if (m64 > (1 << 24) || p64 > (1 << 24) || n64 > (1 << 16)) return GHSVD_ERR_SCRATCH_TOO_SMALL;
+    // shorten (Phase 2) needs working memory of its own: not available here
     if (o.block_width < 1 || o.block_width > hz::KKMAX / 2 || o.inner_sweeps < 1 ||
         o.inner_sweeps > 30 || o.max_sweeps < 1 || o.max_sweeps > 1000 ||
         (o.crit_mode != 0 && o.crit_mode != 1) || o.precision != GHSVD_PRECISION_FP64 ||
-        !(o.tol_scale > 0.0 && o.tol_scale < 1e300))
+        o.ordering != GHSVD_ORDER_ROUND_ROBIN || o.shorten != 0 || o.timeout_ms < 0 ||
+        o.gram_chunk < 0 || !(o.tol_scale > 0.0 && o.tol_scale < 1e300))
         return GHSVD_ERR_INVALID_ARG;
     const int m = (int)m64, p = (int)p64, n = (int)n64;
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GHSVD_ERR_CUDA;
+    // every pointer, J included, must be device memory of the current device;
+    // checked before anything is queued or the shared array is touched
     cudaPointerAttributes pa;
-    for (const void *ptr : {F, G, (const void *)lambda, (const void *)V}) {
+    for (const void *ptr : {F, G, (const void *)lambda, (const void *)V, (const void *)J}) {
         if (!ptr) continue;
         if (cudaPointerGetAttributes(&pa, ptr) != cudaSuccess || pa.type != cudaMemoryTypeDevice ||
             pa.device != dev) {
@@ -187,14 +195,6 @@ extern "C" ghsvd_status ghsvd_solve_noalloc(int64_t m64, int64_t p64, int64_t n6
         noalloc_slots_kernel<<<(total + 255) / 256, 256, 0, st>>>(slotcol, nb, wb, wide);
         NA_TRY(cudaGetLastError());
     }
-    // a host J is read by the sign kernel only through a device copy, which
-    // would need a buffer of the caller's: J must be in device memory
-    if (J) {
-        if (cudaPointerGetAttributes(&pa, J) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
-            cudaGetLastError();
-            return GHSVD_ERR_INVALID_ARG;
-        }
-    }
     NA_TRY(hz::launch_signs(Jrow, J, m, m_pad, n_plus, err + 1, st));
     NA_TRY(hz::launch_copyin(W, false, Mt, m, p, n, m_pad, p_pad, n_pad, F, ldf, G, ldg, nullptr, 0,
                              err, st));
@@ -218,6 +218,13 @@ extern "C" ghsvd_status ghsvd_solve_noalloc(int64_t m64, int64_t p64, int64_t n6
         ia.inner_sweeps = o.inner_sweeps; ia.crit_mode = o.crit_mode;
         ia.tol = o.tol_scale * ldexp(1.0, -53) * sqrt((double)n);
         while (sweeps < o.max_sweeps) {
+            // the wall-time limit, checked between sweeps as in ghsvd_solve
+            if (o.timeout_ms > 0 && sweeps > 0 &&
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                        .count() >= (double)o.timeout_ms) {
+                status = GHSVD_ERR_TIMEOUT;
+                break;
+            }
             NA_TRY(cudaMemsetAsync(counters, 0, 16, st));
             for (int r = 0; r < nsteps; ++r) {
                 sa.slotcol = slotcol + (size_t)r * npairs * kk;
@@ -231,6 +238,7 @@ extern "C" ghsvd_status ghsvd_solve_noalloc(int64_t m64, int64_t p64, int64_t n6
             NA_TRY(cudaMemcpyAsync(herr, err, 8, cudaMemcpyDeviceToHost, st));
             NA_TRY(cudaStreamSynchronize(st));
             ++sweeps;
+            if (sweeps_out) *sweeps_out = sweeps;
             if (herr[0] & hz::DEVERR_RANK) return GHSVD_ERR_RANK_DEFICIENT;
             if (herr[0] & hz::DEVERR_NONFINITE) return GHSVD_ERR_NONFINITE;
             if (hc[1] == 0) { status = GHSVD_OK; break; }

@@ -36,17 +36,18 @@ def dev(gh, X):
     return gh.colmajor(torch.from_numpy(np.asarray(X))).cuda()
 
 
-def noalloc_call(gh, F, G, J, w):
+def noalloc_call(gh, F, G, J, w, host_j=False, **kw):
     """Direct C-ABI call: outputs are allocated here, by the test."""
     lib = gh.load()
     m, n = F.shape
     p = G.shape[0]
     Fd, Gd = dev(gh, F), dev(gh, G)
-    Jd = torch.from_numpy(np.asarray(J, dtype=np.int8)).cuda()
-    lam = torch.empty(n, dtype=torch.float64, device="cuda")
+    Jh = torch.from_numpy(np.ascontiguousarray(J, dtype=np.int8))
+    Jd = Jh if host_j else Jh.cuda()
+    lam = torch.full((n,), 7.0, dtype=torch.float64, device="cuda")
     V = torch.empty_strided((n, n), (1, n), dtype=torch.complex128, device="cuda")
-    opts = gh.ghsvd_default_opts(block_width=w)
-    sweeps = ctypes.c_int(0)
+    opts = gh.ghsvd_default_opts(block_width=w, **kw)
+    sweeps = ctypes.c_int(-1)
     torch.cuda.synchronize()
     s = lib.ghsvd_solve_noalloc(m, p, n, Fd.data_ptr(), m, Jd.data_ptr(), 0, Gd.data_ptr(), p,
                                 lam.data_ptr(), V.data_ptr(), n, ctypes.byref(opts),
@@ -55,8 +56,8 @@ def noalloc_call(gh, F, G, J, w):
     return s, lam.cpu().numpy(), V.cpu().numpy(), sweeps.value
 
 
-def allocating_call(gh, F, G, J, w):
-    s = gh.Solver(0, block_width=w)
+def allocating_call(gh, F, G, J, w, **kw):
+    s = gh.Solver(0, block_width=w, **kw)
     m, n = F.shape
     p = G.shape[0]
     lam, V, sweeps, st = s.solve(dev(gh, F), dev(gh, G),
@@ -96,3 +97,41 @@ def test_noalloc_rejects_problems_beyond_the_array(gh):
     assert s == gh.GHSVD_ERR_SCRATCH_TOO_SMALL
     assert "scratch" in gh.status_string(s)
     assert bool(torch.all(lam == 7.0))
+
+
+def test_noalloc_not_converged_matches_allocating_solve(gh):
+    # one sweep only: GHSVD_ERR_NOT_CONVERGED, one sweep reported, and lambda
+    # and V still written from the factors after that sweep, as ghsvd_solve does
+    F, J, G = P.single_pencil_64()
+    s, lam, V, sweeps = noalloc_call(gh, F, G, J, 8, max_sweeps=1)
+    ref = allocating_call(gh, F, G, J, 8, max_sweeps=1)
+    assert s == gh.GHSVD_ERR_NOT_CONVERGED and ref["status"] == gh.GHSVD_ERR_NOT_CONVERGED
+    assert sweeps == 1 and ref["sweeps"] == 1
+    np.testing.assert_array_equal(lam, ref["lam"])
+    np.testing.assert_array_equal(V, ref["V"])
+
+
+def test_noalloc_rejects_host_j_shorten_and_other_orderings(gh):
+    F, J, G = P.single_pencil_64()
+    for kw, host_j in ((dict(), True), (dict(shorten=1), False), (dict(ordering=1), False)):
+        s, lam, _, sweeps = noalloc_call(gh, F, G, J, 8, host_j=host_j, **kw)
+        assert s == gh.GHSVD_ERR_INVALID_ARG, kw
+        assert sweeps == 0                      # written on every return
+        assert np.all(lam == 7.0)               # nothing queued, outputs untouched
+    # a rejected call leaves nothing behind: the next call solves as before
+    s, lam, _, sweeps = noalloc_call(gh, F, G, J, 8)
+    ref = allocating_call(gh, F, G, J, 8)
+    assert s == gh.GHSVD_OK and sweeps == ref["sweeps"]
+    tol = eig_tol_vec(F, G, J, ref["lam"], ref["F"])
+    assert np.all(rel_err(lam, ref["lam"]) < tol)
+
+
+def test_noalloc_honours_the_time_limit(gh):
+    # the n = 256 pencil takes dozens of sweeps of 31 steps at block width 8;
+    # a 1 ms limit passes long before that: the call stops between sweeps with
+    # GHSVD_ERR_TIMEOUT and the outputs of the current factors
+    F, J, G = P.lapw_pencil(256)
+    s, lam, _, sweeps = noalloc_call(gh, F, G, J, 8, timeout_ms=1)
+    assert s == gh.GHSVD_ERR_TIMEOUT
+    assert sweeps >= 1
+    assert np.all(np.isfinite(lam)) and not np.all(lam == 7.0)
