@@ -115,9 +115,17 @@ typedef struct {
                             that of the tall pencil and V is returned in the
                             caller's column order (rows permuted back by P2).
                             Not with a warm start.  0 (default): the tall
-                            factors.  ghsvd_solve_batched and
-                            ghsvd_solve_noalloc ignore it (and timeout_ms;
-                            they use tol_scale).                               */
+                            factors.  ghsvd_solve_batched ignores it (and
+                            timeout_ms; it uses tol_scale);
+                            ghsvd_solve_noalloc rejects shorten = 1 and
+                            honours timeout_ms.                                */
+    int mixed_tc;        /* GHSVD_PRECISION_MIXED: 1 runs the Grams and block
+                            updates of the complex64 sweeps on the tensor
+                            cores (tcgen05, TF32 operands split into high and
+                            low parts, three products per real product, FP32
+                            accumulation); 0 (default) on the FP32 CUDA cores.
+                            The 2x2 parameters, J-norms and stopping test are
+                            FP64 either way.                                  */
 } ghsvd_opts;
 
 /* Per-solve statistics (Section 6.4.3, "Completing a sweep"). */
@@ -136,6 +144,7 @@ typedef struct {
     int rounds_low;                /* complex64 rounds (mixed schedule)          */
     double ms_phase2;              /* wall time of Phase 2 in the solve (shorten) */
     int n2x2;                      /* 2x2 pivots of that Phase 2                 */
+    int sweeps_tc;                 /* complex64 sweeps run on the tensor cores   */
 } ghsvd_stats;
 
 /* Fill *opts with the defaults listed above. */
@@ -302,6 +311,27 @@ ghsvd_status ghsvd_s_orthonormalize(int count, int64_t p, int64_t n, const void 
 ghsvd_status ghsvd_align_phases(int64_t n, const void *Vref, int64_t ldr, void *V, int64_t ldv,
                                 void *stream);
 
+/*
+ * The tensor-core block operations of the complex64 sweeps (opts.mixed_tc) on
+ * one block pair, for verification against a reference: the block-pivot Gram
+ * of Section 6.4.2 (eq. 6.1), gram = X^* J X (J = NULL: X^* X), and the block
+ * update of Section 6.4.3, X <- X Z, both by tcgen05.mma of kind::tf32 (each
+ * real product as hi*hi + hi*lo + lo*hi of TF32 parts, FP32 accumulation;
+ * the update in the delta form X + X (Z - I), X added in FP32).
+ *   X     device, complex64 (two floats), rows x 64, column-major, ldx = rows,
+ *         rows a positive multiple of 64; overwritten by X Z
+ *   J     device int8, rows entries +-1, or NULL
+ *   Z     device, complex64 64 x 64, column-major (ld 64); a column equal to
+ *         e_j leaves column j of X exactly as it was
+ *   gram  device, complex64 64 x 64, column-major, written in full (the upper
+ *         part computed, the lower part its conjugate transpose)
+ * Allocates its small temporaries on `stream`; returns INVALID_ARG for bad
+ * sizes, GHSVD_ERR_CUDA if the tensor-core path is not available or a
+ * device-side wait ran out.
+ */
+ghsvd_status ghsvd_tc_block_ops(int64_t rows, void *X, int64_t ldx, const int8_t *J, const void *Z,
+                                void *gram, void *stream);
+
 /* Size of the device array that ghsvd_solve_noalloc works in (32 MiB). */
 #define GHSVD_NOALLOC_SCRATCH_BYTES (32u << 20)
 
@@ -320,15 +350,24 @@ ghsvd_status ghsvd_align_phases(int64_t n, const void *Vref, int64_t ldr, void *
  * are rejected with GHSVD_ERR_SCRATCH_TOO_SMALL (for F 1.5n x n and G 2n x n
  * the limit is about n = 640 at block width 32).
  *
- * Arguments as for ghsvd_solve, except: F, G, lambda, V and a non-NULL J must
- * be device memory of the current device; opts (NULL: defaults) must ask for
- * GHSVD_PRECISION_FP64; the options `timing` and `mixed_max_sweeps` are
- * ignored.
+ * Arguments as for ghsvd_solve, except:
+ *   - F, G, lambda, V and a non-NULL J must be device memory of the current
+ *     device (a host J, or memory of another device, is GHSVD_ERR_INVALID_ARG,
+ *     returned before anything is queued);
+ *   - opts (NULL: defaults) must ask for GHSVD_PRECISION_FP64, the round-robin
+ *     ordering and shorten = 0 (Phase 2 needs working memory of its own);
+ *     anything else is GHSVD_ERR_INVALID_ARG.  block_width 0 means 32;
+ *     timeout_ms is honoured between sweeps as in ghsvd_solve; `timing`,
+ *     `mixed_max_sweeps` and `mixed_param32` are ignored.
+ * *sweeps (if non-NULL) is written on every return: 0 before the iteration,
+ * else the sweeps run.  lambda and V are written on GHSVD_OK,
+ * GHSVD_ERR_NOT_CONVERGED and GHSVD_ERR_TIMEOUT.
  *
  * The first call on a device looks up the array's device address and sets
  * the kernels' shared-memory limits for that device; make that first call
- * before any stream capture.  Every call shares the array and clears the
- * parts that must start at zero; calls that overlap on the GPU (other
+ * before any stream capture begins.  Every call waits on `stream` after each
+ * sweep to read the sweep's counters.  Every call shares the array and clears
+ * the parts that must start at zero; calls that overlap on the GPU (other
  * streams, other host threads) race on it and must be ordered by the caller.
  */
 ghsvd_status ghsvd_solve_noalloc(int64_t m, int64_t p, int64_t n,

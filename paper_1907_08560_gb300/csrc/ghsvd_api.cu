@@ -216,7 +216,7 @@ ghsvd_status ghsvd_create(ghsvd_t *out, int device, const ghsvd_opts *opts)
         (o.precision != GHSVD_PRECISION_FP64 && o.precision != GHSVD_PRECISION_MIXED) ||
         o.mixed_max_sweeps < 0 || o.gram_chunk < 0 || (o.timing != 0 && o.timing != 1) ||
         (o.shorten != 0 && o.shorten != 1) || o.ordering != GHSVD_ORDER_ROUND_ROBIN ||
-        (o.mixed_param32 != 0 && o.mixed_param32 != 1) ||
+        (o.mixed_param32 != 0 && o.mixed_param32 != 1) || (o.mixed_tc != 0 && o.mixed_tc != 1) ||
         !(o.tol_scale > 0.0 && o.tol_scale < 1e300) || o.timeout_ms < 0)
         return GHSVD_ERR_INVALID_ARG;
     int ndev = 0;
@@ -295,7 +295,12 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
     const bool mixed = o.precision == GHSVD_PRECISION_MIXED && n >= 2;
     const int kc = n >= 2 ? choose_chunk(m_pad, p_pad, npairs, h->num_sms, o.gram_chunk) : 16;
     const int chunks_h = (m_pad + kc - 1) / kc, chunks_s = (p_pad + kc - 1) / kc;
-    const int cpp = chunks_h + chunks_s;
+    // the complex64 sweeps on the tensor cores (opts.mixed_tc) have a row
+    // chunk of their own (two Gram CTAs per SM)
+    const bool use_tc = mixed && o.mixed_tc && hz::tc_supported(kk, npairs, Mt);
+    const int kc_tc = use_tc ? hz::tc_gram_chunk_rows(m_pad, p_pad, npairs, h->num_sms) : kc;
+    const int chunks_h_tc = (m_pad + kc_tc - 1) / kc_tc, chunks_s_tc = (p_pad + kc_tc - 1) / kc_tc;
+    const int cpp = std::max(chunks_h + chunks_s, chunks_h_tc + chunks_s_tc);
 
     // buffers
     long long cap;
@@ -417,8 +422,10 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
         StepArgs sa{};
         sa.npairs = npairs; sa.kk = kk; sa.m_pad = m_pad; sa.p_pad = p_pad; sa.n_pad = n_pad;
         sa.ld = Mt; sa.kc = kc; sa.chunks_h = chunks_h; sa.chunks_s = chunks_s;
+        StepArgs sa_tc = sa;
+        sa_tc.kc = kc_tc; sa_tc.chunks_h = chunks_h_tc; sa_tc.chunks_s = chunks_s_tc;
         InnerArgs ia{};
-        ia.npairs = npairs; ia.kk = kk; ia.cpp = cpp; ia.chunks_h = chunks_h;
+        ia.npairs = npairs; ia.kk = kk; ia.cpp = chunks_h + chunks_s; ia.chunks_h = chunks_h;
         ia.inner_sweeps = o.inner_sweeps; ia.crit_mode = o.crit_mode;
         ia.param32 = o.mixed_param32;
         const double tol64 = o.tol_scale * ldexp(1.0, -53) * sqrt((double)n);
@@ -456,7 +463,10 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
                 break;
             }
             const bool single = phase_single != 0;
+            const bool tcs = single && use_tc;
             ia.tol = single ? tol32 : tol64;
+            ia.cpp = tcs ? chunks_h_tc + chunks_s_tc : chunks_h + chunks_s;
+            ia.chunks_h = tcs ? chunks_h_tc : chunks_h;
             CUDA_TRY(cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned long long), st));
             const bool timed = o.timing != 0;
             if (timed) CUDA_TRY(h->timer.reserve(6 * nsteps));
@@ -465,14 +475,22 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
                 void *Wc = single ? (void *)h->W32 : (void *)h->W;
                 sa.slotcol = h->slotcol + (size_t)r * npairs * kk;
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 0], st));
-                CUDA_TRY(hz::launch_gram(Wc, single, h->Jrow, sa, h->partial, st));
+                if (tcs) {
+                    sa_tc.slotcol = sa.slotcol;
+                    CUDA_TRY(hz::launch_gram_tc(Wc, h->Jrow, sa_tc, n, h->partial, h->err, st));
+                } else {
+                    CUDA_TRY(hz::launch_gram(Wc, single, h->Jrow, sa, h->partial, st));
+                }
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 1], st));
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 2], st));
                 CUDA_TRY(hz::launch_inner(h->partial, single, sa.slotcol, ia, h->zhat, h->pair_flag,
                                           h->counters, h->err, st));
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 3], st));
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 4], st));
-                CUDA_TRY(hz::launch_update(Wc, single, sa, h->zhat, h->pair_flag, st));
+                if (tcs)
+                    CUDA_TRY(hz::launch_update_tc(Wc, sa, n, h->zhat, h->pair_flag, h->err, h->num_sms, st));
+                else
+                    CUDA_TRY(hz::launch_update(Wc, single, sa, h->zhat, h->pair_flag, st));
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 5], st));
             }
             h->stats.launches_gram += nsteps;
@@ -500,6 +518,8 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
             }
             ++sweeps;
             if (single) ++sweeps_low;
+            if (tcs) ++h->stats.sweeps_tc;
+            if (h->h_err[0] & hz::DEVERR_TIMEOUT) { status = GHSVD_ERR_CUDA; break; }
             if (h->h_err[0] & hz::DEVERR_RANK) { status = GHSVD_ERR_RANK_DEFICIENT; break; }
             if (h->h_err[0] & hz::DEVERR_NONFINITE) { status = GHSVD_ERR_NONFINITE; break; }
             if (single) {
@@ -536,7 +556,8 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
     h->stats.sweeps = sweeps;
     h->stats.sweeps_low = sweeps_low;
     h->stats.rounds_low = rounds;
-    if (status == GHSVD_ERR_RANK_DEFICIENT || status == GHSVD_ERR_NONFINITE) return status;
+    if (status == GHSVD_ERR_RANK_DEFICIENT || status == GHSVD_ERR_NONFINITE || status == GHSVD_ERR_CUDA)
+        return status;
 
     // outputs (Section 6.1.7)
     CUDA_TRY(hz::launch_finalize(h->W, Mt, h->Jrow, m_pad, p_pad, n, o.sort_ascending, h->lam_tmp,

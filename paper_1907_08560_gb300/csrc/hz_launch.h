@@ -89,6 +89,7 @@ inline int gram_chunk_rows(int m_pad, int p_pad, int npairs, int sms)
 // Error flags raised by the device (bitwise or).
 constexpr int DEVERR_RANK = 1;
 constexpr int DEVERR_NONFINITE = 2;
+constexpr int DEVERR_TIMEOUT = 4;     // a bounded device-side wait ran out
 
 // One item of a batched FP64 product C = A B (A rows x n, B n x n, C rows x n,
 // column-major); the batched copy uses A as source and C as destination.
@@ -139,6 +140,18 @@ cudaError_t launch_gemm(const double2 *A, long long lda, int rows, const void *B
 cudaError_t launch_eye32(void *W, long long ld, int r0, int n, int n_pad, cudaStream_t s);
 cudaError_t launch_extract(const double2 *W, long long ld, int r0, int rows, int n, double2 *out,
                            long long ldo, cudaStream_t s);
+
+// Tensor-core (tcgen05 TF32) Gram and update of the complex64 sweeps (hz_tc.cu).
+// W32 is the complex64 working copy; partial holds complex64 partials in the
+// layout of launch_gram; zhat the complex64 Z^ of launch_inner.  Device waits
+// are bounded: a wait that runs out raises DEVERR_TIMEOUT in err[0].
+bool tc_supported(int kk, int npairs, long long ld);
+int tc_gram_chunk_rows(int m_pad, int p_pad, int npairs, int sms);
+cudaError_t tc_setup();
+cudaError_t launch_gram_tc(const void *W32, const int8_t *Jrow, const StepArgs &a, int n, void *partial,
+                           int *err, cudaStream_t s);
+cudaError_t launch_update_tc(void *W32, const StepArgs &a, int n, const double2 *zhat, const int *pair_flag,
+                             int *err, int sms, cudaStream_t s);
 
 // Phase 2 (hz_urv.cu): the (J, I) URV shortening of Section 5.
 size_t urv_workspace_bytes(long long m, long long p, int n);

@@ -550,6 +550,8 @@ cudaError_t setup_kernels()
     e = cudaFuncSetAttribute(update_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)update_smem(sizeof(float2)));
     if (e != cudaSuccess) return e;
+    e = tc_setup();
+    if (e != cudaSuccess) return e;
     if (g_cluster_mask < 0) {
         int m64 = 0, m32 = 0;
         const char *env = getenv("GHSVD_INNER_CLUSTER");

@@ -40,7 +40,8 @@ class ghsvd_opts(ctypes.Structure):
                 ("sort_ascending", ctypes.c_int), ("gram_chunk", ctypes.c_int),
                 ("timing", ctypes.c_int), ("ordering", ctypes.c_int),
                 ("tol_scale", ctypes.c_double), ("timeout_ms", ctypes.c_int64),
-                ("mixed_param32", ctypes.c_int), ("shorten", ctypes.c_int)]
+                ("mixed_param32", ctypes.c_int), ("shorten", ctypes.c_int),
+                ("mixed_tc", ctypes.c_int)]
 
 
 class ghsvd_stats(ctypes.Structure):
@@ -53,7 +54,7 @@ class ghsvd_stats(ctypes.Structure):
                 ("launches_update", ctypes.c_longlong), ("ms_gram", ctypes.c_double),
                 ("ms_inner", ctypes.c_double), ("ms_update", ctypes.c_double),
                 ("rounds_low", ctypes.c_int), ("ms_phase2", ctypes.c_double),
-                ("n2x2", ctypes.c_int)]
+                ("n2x2", ctypes.c_int), ("sweeps_tc", ctypes.c_int)]
 
 
 class GhsvdError(RuntimeError):
@@ -94,6 +95,8 @@ def load(path: str | None = None):
     lib.ghsvd_get_factors.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp]
     lib.ghsvd_get_stats.restype = c_int
     lib.ghsvd_get_stats.argtypes = [vp, ctypes.POINTER(ghsvd_stats)]
+    lib.ghsvd_tc_block_ops.restype = c_int
+    lib.ghsvd_tc_block_ops.argtypes = [i64, vp, i64, vp, vp, vp, vp]
     lib.ghsvd_solve_noalloc.restype = c_int
     lib.ghsvd_solve_noalloc.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, i64,
                                         ctypes.POINTER(ghsvd_opts), ctypes.POINTER(c_int), vp]
@@ -472,6 +475,22 @@ def ghsvd_s_orthonormalize(Gs, V0s, stream=None):
     return V0s
 
 
+def ghsvd_tc_block_ops(X, J, Z, stream=None):
+    """The tensor-core Gram and update of the complex64 sweeps on one block
+    pair (include/ghsvd.h): X (rows x 64 complex64 column-major CUDA tensor,
+    rows a multiple of 64) is overwritten by X Z; returns gram = X^* J X
+    (64 x 64 complex64, J an int8 CUDA tensor or None)."""
+    import torch
+    if X.dtype != torch.complex64 or Z.dtype != torch.complex64:
+        raise TypeError("ghsvd_tc_block_ops works on complex64 tensors")
+    rows = X.shape[0]
+    gram = torch.empty_strided((64, 64), (1, 64), dtype=torch.complex64, device=X.device)
+    Jp = None if J is None else ctypes.c_void_p(J.contiguous().data_ptr())
+    _check(load().ghsvd_tc_block_ops(rows, X.data_ptr(), ld_of(X), Jp, Z.data_ptr(), gram.data_ptr(),
+                                      _stream_ptr(stream)))
+    return gram
+
+
 def ghsvd_align_phases(Vref, V, stream=None):
     """In place: align the phase of each column of V to the same column of Vref."""
     _check(load().ghsvd_align_phases(V.shape[1], Vref.data_ptr(), ld_of(Vref), V.data_ptr(),
@@ -500,7 +519,8 @@ def ghsvd_get_stats(h) -> dict:
                 kernel_launches=st.kernel_launches, launches_gram=st.launches_gram,
                 launches_inner=st.launches_inner, launches_update=st.launches_update,
                 ms_gram=st.ms_gram, ms_inner=st.ms_inner, ms_update=st.ms_update,
-                rounds_low=st.rounds_low, ms_phase2=st.ms_phase2, n2x2=st.n2x2)
+                rounds_low=st.rounds_low, ms_phase2=st.ms_phase2, n2x2=st.n2x2,
+                sweeps_tc=st.sweeps_tc)
 
 
 def ghsvd_urv(F, J, G, n_plus: int | None = None, stream=None):

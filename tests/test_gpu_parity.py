@@ -254,17 +254,20 @@ def test_mixed_precision_schedule(gh):
     check_eigs(F, G, J, gpu, ref)
 
 
-@pytest.mark.parametrize("precision,param32", [(0, 0), (1, 0), (1, 1)])
-def test_lapw_shaped_pencil_256_matches_oracle(gh, precision, param32):
+@pytest.mark.parametrize("precision,param32,tc", [(0, 0, 0), (1, 0, 0), (1, 1, 0), (1, 0, 1),
+                                                   (1, 1, 1)])
+def test_lapw_shaped_pencil_256_matches_oracle(gh, precision, param32, tc):
     # the benchmark's pencil family at n = 256 (F 384 x 256 with 64 negative
     # signs, G 512 x 256, cond(S) = 1e10), FP64 and mixed schedules (the
-    # complex64 sweeps with FP64 or FP32 2x2 parameters)
+    # complex64 sweeps with FP64 or FP32 2x2 parameters, their Grams and
+    # updates on the CUDA cores or on the tensor cores)
     F, J, G = P.lapw_pencil(256)
     ref = oracle.solve(F, G, J, method="blocked", w=32)
     assert ref["status"] == 0
     gpu = gpu_solve(gh, F, G, J, block_width=32, precision=precision, max_sweeps=80,
-                    mixed_param32=param32)
+                    mixed_param32=param32, mixed_tc=tc)
     assert gpu["status"] == 0
     if precision:
         assert gpu["stats"]["sweeps_low"] > 0
+    assert gpu["stats"]["sweeps_tc"] == (gpu["stats"]["sweeps_low"] if tc else 0)
     check_eigs(F, G, J, gpu, ref)
