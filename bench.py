@@ -31,9 +31,12 @@ sys.path.insert(0, ROOT)
 METRIC = "HZ GHSVD solves/s at n=2048 c128"
 N, M, P, M_MINUS, W_BLOCK = 2048, 3072, 4096, 512, 32
 SEED = 1907085600 + 2
-# Outer sweeps the FP64 GPU solve of this pencil takes (measured; the CPU
-# reference arm extrapolates its timed sample with it).
-SWEEPS_PER_SOLVE = 36
+# Outer sweeps the FP64 GPU solve of the LAPW-shaped pencil takes, by order
+# (measured; the CPU reference arm extrapolates its timed sample with it).
+# The blocked FP64 oracle takes the same 36 sweeps at n = 2048 (a whole
+# oracle solve, tests/golden/fullsize_oracle.json).
+SWEEPS_BY_ORDER = {2048: 36, 4096: 37}
+SWEEPS_PER_SOLVE = SWEEPS_BY_ORDER[2048]
 # C_max: this ill-conditioned pencil needs more than the paper's ~30 sweeps
 MAX_SWEEPS = 80
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
@@ -293,12 +296,15 @@ def run_reference(args, rank, world):
         oracle.time_blocked_steps(F, G, J, w=W_BLOCK, target_s=0.0, nthreads=nthreads, max_steps=1)
     t_step, steps = oracle.time_blocked_steps(F, G, J, w=W_BLOCK, target_s=0.0,
                                               nthreads=nthreads, max_steps=args.steps)
-    solve_s = t_step * steps_per_sweep * SWEEPS_PER_SOLVE
+    sweeps = SWEEPS_BY_ORDER.get(N, SWEEPS_PER_SOLVE)
+    how = ("measured for this order" if N in SWEEPS_BY_ORDER else
+           f"ASSUMED: the sweep count of the n=2048 pencil, not measured at n={N}")
+    solve_s = t_step * steps_per_sweep * sweeps
     value = 1.0 / solve_s
     sample = (f"each step: one outer step ({N // W_BLOCK // 2} block pairs) of the FP64 blocked "
               f"oracle at n={N} "
               f"on {oracle.max_threads()} host threads ({t_step:.3f} s); solve time extrapolated "
-              f"x {steps_per_sweep} steps/sweep x {SWEEPS_PER_SOLVE} sweeps")
+              f"x {steps_per_sweep} steps/sweep x {sweeps} sweeps ({how})")
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -613,7 +619,7 @@ def main():
         torch.cuda.synchronize()
         ef, eg = solver.decomposition_errors(Fd, Gd, X, stream=stream)
         phase4 = {"ms": q0.elapsed_time(q1), "err_F_eq7_1": ef, "err_G_eq7_1": eg,
-                  "what": "Sigma_F, Sigma_G and X = Z^{-1} by complete pivoting (n = 2048)"}
+                  "what": f"Sigma_F, Sigma_G and X = Z^{{-1}} by complete pivoting (n = {N})"}
         del sf, sg, X
 
     # speedup of the mixed-precision schedule over the FP64 solve at equal
@@ -641,6 +647,7 @@ def main():
         mixed = {"value": mvalue, "unit": "solves/s", "ms_per_step": mixed_ms / args.mixed_steps,
                  "speedup_vs_fp64": mvalue / value, "status": mst,
                  "sweeps_complex64": ms_stats["sweeps_low"],
+                 "sweeps_complex64_tensor_cores": ms_stats["sweeps_tc"],
                  "sweeps_fp64": ms_stats["sweeps"] - ms_stats["sweeps_low"],
                  "rounds_complex64": ms_stats["rounds_low"],
                  "eig_rel_diff_vs_fp64_max": emax,
@@ -666,26 +673,32 @@ def main():
                                 "status": st_ms, "eig_rel_diff_vs_fp64_max": emax,
                                 "eig_rel_diff_over_tol_max": eratio}
         msolver.close()
-        # the same schedule with the complex64 sweeps' 2x2 parameters in FP32
-        msolver = ghsvd.Solver(local, block_width=W_BLOCK, precision=ghsvd.GHSVD_PRECISION_MIXED,
-                               max_sweeps=args.max_sweeps, mixed_max_sweeps=60, mixed_param32=1)
-        msolver.solve(Fd, Gd, Jd, stream=stream)          # warm-up
-        torch.cuda.synchronize()
-        m0.record(stream)
-        for _ in range(args.mixed_steps):
-            lam_mf, _, _, st_mf = msolver.solve(Fd, Gd, Jd, stream=stream)
-        m1.record(stream)
-        torch.cuda.synchronize()
-        mf_ms = allreduce(m0.elapsed_time(m1), dist.ReduceOp.MAX if dist else None)
-        emax, eratio = eig_vs_fp64(lam_mf)
-        sst_f = msolver.stats()
-        mvalue3 = world * args.mixed_steps / (mf_ms / 1e3)
-        mixed["with_fp32_parameters"] = {"value": mvalue3, "speedup_vs_fp64": mvalue3 / value,
-                                         "sweeps_complex64": sst_f["sweeps_low"],
-                                         "sweeps_fp64": sst_f["sweeps"] - sst_f["sweeps_low"],
-                                         "status": st_mf, "eig_rel_diff_vs_fp64_max": emax,
-                                         "eig_rel_diff_over_tol_max": eratio}
-        msolver.close()
+        # variants: the complex64 sweeps' 2x2 parameters in FP32, and the
+        # complex64 Grams and updates on the FP32 CUDA cores instead of the
+        # tensor cores (the default), with either parameter precision
+        for key, kw in (("with_fp32_parameters", dict(mixed_param32=1)),
+                        ("with_cuda_cores", dict(mixed_tc=0)),
+                        ("with_fp32_parameters_cuda_cores", dict(mixed_param32=1, mixed_tc=0))):
+            msolver = ghsvd.Solver(local, block_width=W_BLOCK, precision=ghsvd.GHSVD_PRECISION_MIXED,
+                                   max_sweeps=args.max_sweeps, mixed_max_sweeps=60, **kw)
+            msolver.solve(Fd, Gd, Jd, stream=stream)          # warm-up
+            torch.cuda.synchronize()
+            m0.record(stream)
+            for _ in range(args.mixed_steps):
+                lam_mf, _, _, st_mf = msolver.solve(Fd, Gd, Jd, stream=stream)
+            m1.record(stream)
+            torch.cuda.synchronize()
+            mf_ms = allreduce(m0.elapsed_time(m1), dist.ReduceOp.MAX if dist else None)
+            emax, eratio = eig_vs_fp64(lam_mf)
+            sst_f = msolver.stats()
+            mvalue3 = world * args.mixed_steps / (mf_ms / 1e3)
+            mixed[key] = {"value": mvalue3, "speedup_vs_fp64": mvalue3 / value,
+                          "sweeps_complex64": sst_f["sweeps_low"],
+                          "sweeps_complex64_tensor_cores": sst_f["sweeps_tc"],
+                          "sweeps_fp64": sst_f["sweeps"] - sst_f["sweeps_low"],
+                          "status": st_mf, "eig_rel_diff_vs_fp64_max": emax,
+                          "eig_rel_diff_over_tol_max": eratio}
+            msolver.close()
 
     # Phase 2 first (the square factors of the (J, I) URV factorization), then
     # the FP64 iteration on them; eigenvectors mapped back to the tall pencil

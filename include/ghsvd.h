@@ -119,11 +119,15 @@ typedef struct {
                             timeout_ms; it uses tol_scale);
                             ghsvd_solve_noalloc rejects shorten = 1 and
                             honours timeout_ms.                                */
-    int mixed_tc;        /* GHSVD_PRECISION_MIXED: 1 runs the Grams and block
-                            updates of the complex64 sweeps on the tensor
-                            cores (tcgen05, TF32 operands split into high and
-                            low parts, three products per real product, FP32
-                            accumulation); 0 (default) on the FP32 CUDA cores.
+    int mixed_tc;        /* GHSVD_PRECISION_MIXED: 1 (default) runs the Grams
+                            of the complex64 sweeps on the tensor cores
+                            (tcgen05, TF32 operands split into high and low
+                            parts, three products per real product, FP32
+                            accumulation) and the block update of every pair
+                            whose Z^ - I is small (all entries <= 1/2) there
+                            too, in the delta form X + X (Z^ - I); pairs with
+                            larger rotations are updated on the FP32 CUDA
+                            cores.  0: Grams and updates on the CUDA cores.
                             The 2x2 parameters, J-norms and stopping test are
                             FP64 either way.                                  */
 } ghsvd_opts;
@@ -145,6 +149,10 @@ typedef struct {
     double ms_phase2;              /* wall time of Phase 2 in the solve (shorten) */
     int n2x2;                      /* 2x2 pivots of that Phase 2                 */
     int sweeps_tc;                 /* complex64 sweeps run on the tensor cores   */
+    long long batch_ticks;         /* ghsvd_solve_batched: ticks (one outer step
+                                      of every active pencil) run on the device  */
+    int batch_graph_launches;      /* ghsvd_solve_batched: launches of the solve's
+                                      graph (its while loop runs on the device)  */
 } ghsvd_stats;
 
 /* Fill *opts with the defaults listed above. */
@@ -227,8 +235,12 @@ void ghsvd_destroy(ghsvd_t h);
  * its own block schedule (Section 6.4.1, 6.3) and stopping rule (no big
  * transformation in its sweep, Section 6.1.7); one outer step of every
  * pencil that has not stopped runs per "tick" (a Gram, an inner and an
- * update kernel over all pencils, and a control kernel on the device), and
- * the ticks are replayed as a CUDA graph until every pencil has stopped.
+ * update kernel over all pencils, and a control kernel on the device).  The
+ * whole iteration is one launch of a CUDA graph whose conditional while node
+ * repeats the tick; the control kernel decides on the device whether another
+ * tick runs (some pencil active, fewer than max_sweeps sweeps of the longest
+ * schedule), so the host waits once (ghsvd_stats.batch_ticks,
+ * batch_graph_launches).
  *   m, p, n       host arrays [batch]: sizes of pencil i (n_i >= 2).
  *   F, G          host arrays [batch] of device pointers (complex128,
  *                 column-major) with host arrays ldf, ldg [batch].

@@ -58,6 +58,7 @@ struct ghsvd_ctx {
     void *partial = nullptr;            // Gram partials (FP64 or FP32 pairs)
     double2 *zhat = nullptr;            // [pairs][KKMAX^2] accumulated block transforms
     int *pair_flag = nullptr;           // [pairs]
+    int *route = nullptr;               // [2][pairs]: tensor-core / CUDA-core update of a pair
     int *slotcol = nullptr;             // [steps][pairs][kk]
     int8_t *Jrow = nullptr;             // [m_pad]
     int8_t *Jdev = nullptr;             // [m] staging of a host J
@@ -117,12 +118,12 @@ static void free_all(ghsvd_ctx *h)
     cudaFree(h->d_item);
     h->d_item = nullptr;
     cudaFree(h->W); cudaFree(h->W32); cudaFree(h->Wtmp); cudaFree(h->partial); cudaFree(h->zhat);
-    cudaFree(h->pair_flag); cudaFree(h->slotcol); cudaFree(h->Jrow); cudaFree(h->Jdev);
+    cudaFree(h->pair_flag); cudaFree(h->route); cudaFree(h->slotcol); cudaFree(h->Jrow); cudaFree(h->Jdev);
     cudaFree(h->counters); cudaFree(h->err); cudaFree(h->lam_tmp); cudaFree(h->gscale);
     cudaFree(h->rank); cudaFree(h->vnorm2); cudaFree(h->gcol2); cudaFree(h->kappa);
     cudaFreeHost(h->h_counters); cudaFreeHost(h->h_err);
     h->W = nullptr; h->W32 = nullptr; h->Wtmp = nullptr; h->partial = nullptr; h->zhat = nullptr;
-    h->pair_flag = nullptr; h->slotcol = nullptr; h->Jrow = nullptr; h->Jdev = nullptr;
+    h->pair_flag = nullptr; h->route = nullptr; h->slotcol = nullptr; h->Jrow = nullptr; h->Jdev = nullptr;
     h->counters = nullptr; h->err = nullptr; h->lam_tmp = nullptr; h->gscale = nullptr;
     h->rank = nullptr; h->h_counters = nullptr; h->h_err = nullptr;
     h->vnorm2 = nullptr; h->gcol2 = nullptr; h->kappa = nullptr;
@@ -182,6 +183,7 @@ ghsvd_status ghsvd_default_opts(ghsvd_opts *o)
     o->tol_scale = 1.0;
     o->timeout_ms = 0;
     o->shorten = 0;
+    o->mixed_tc = 1;
     return GHSVD_OK;
 }
 
@@ -313,10 +315,11 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
         h->partial = pp;
     }
     if (npairs > h->cap_pairs || h->zhat == nullptr) {
-        cudaFree(h->zhat); cudaFree(h->pair_flag);
-        h->zhat = nullptr; h->pair_flag = nullptr;
+        cudaFree(h->zhat); cudaFree(h->pair_flag); cudaFree(h->route);
+        h->zhat = nullptr; h->pair_flag = nullptr; h->route = nullptr;
         CUDA_TRY(cudaMalloc((void **)&h->zhat, sizeof(double2) * std::max(npairs, 1) * hz::KKMAX * hz::KKMAX));
         CUDA_TRY(cudaMalloc((void **)&h->pair_flag, sizeof(int) * std::max(npairs, 1)));
+        CUDA_TRY(cudaMalloc((void **)&h->route, 2 * sizeof(int) * std::max(npairs, 1)));
         h->cap_pairs = std::max(npairs, 1);
     }
     cap = (long long)h->cap_steps;
@@ -487,16 +490,22 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
                                           h->counters, h->err, st));
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 3], st));
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 4], st));
-                if (tcs)
-                    CUDA_TRY(hz::launch_update_tc(Wc, sa, n, h->zhat, h->pair_flag, h->err, h->num_sms, st));
-                else
+                if (tcs) {
+                    // pairs with small rotations on the tensor cores, the others on
+                    // the CUDA cores (launch_route)
+                    int *tcf = h->route, *ccf = h->route + npairs;
+                    CUDA_TRY(hz::launch_route(h->zhat, h->pair_flag, kk, npairs, tcf, ccf, st));
+                    CUDA_TRY(hz::launch_update_tc(Wc, sa, n, h->zhat, tcf, h->err, h->num_sms, st));
+                    CUDA_TRY(hz::launch_update(Wc, true, sa, h->zhat, ccf, st));
+                } else {
                     CUDA_TRY(hz::launch_update(Wc, single, sa, h->zhat, h->pair_flag, st));
+                }
                 if (timed) CUDA_TRY(cudaEventRecord(ev[6 * r + 5], st));
             }
             h->stats.launches_gram += nsteps;
             h->stats.launches_inner += nsteps;
             h->stats.launches_update += nsteps;
-            h->stats.kernel_launches += 3LL * nsteps;
+            h->stats.kernel_launches += (tcs ? 5LL : 3LL) * nsteps;
             CUDA_TRY(cudaMemcpyAsync(h->h_counters, h->counters, 2 * sizeof(unsigned long long),
                                      cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaMemcpyAsync(h->h_err, h->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -779,10 +788,13 @@ extern "C" ghsvd_status ghsvd_solve_batched(ghsvd_t h, int batch, const int64_t 
     memset(&h->stats, 0, sizeof(h->stats));
     int w = 0;
     double ms = 0;
+    long long ticks = 0;
     ghsvd_status s = hz_batch_solve(h->batch, h->device, &h->opts, batch, m, p, n, F, ldf, J, n_plus,
-                                    G, ldg, V0, ldv0, lambda, V, ldv, sweeps, status, &w, &ms, stream);
+                                    G, ldg, V0, ldv0, lambda, V, ldv, sweeps, status, &w, &ms, &ticks, stream);
     h->stats.block_width = w;
     h->stats.ms_total = ms;
+    h->stats.batch_ticks = ticks;
+    h->stats.batch_graph_launches = ticks > 0 ? 1 : 0;
     h->solved = false;          // ghsvd_get_factors refers to single solves
     cudaSetDevice(prev);
     return s;

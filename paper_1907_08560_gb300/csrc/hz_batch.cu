@@ -8,9 +8,10 @@
 // Gram, inner and update kernels over the work items of every pencil (CTAs of
 // inactive pencils return at once), and a control kernel that advances each
 // pencil's step and, at the end of its sweep, applies the stopping rule of
-// Section 6.1.7 to that pencil's own counters.  The ticks are captured in a
-// CUDA graph and replayed until no pencil is active, so the host only reads
-// one counter per replay.
+// Section 6.1.7 to that pencil's own counters.  The whole iteration is one
+// launch of a CUDA graph whose conditional while node repeats the tick: the
+// control kernel sets the loop condition on the device, and the host waits
+// once, when no pencil is active any more.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -105,10 +106,14 @@ update_batched(const BPencil *__restrict__ P, const BState *__restrict__ S, cons
 
 // One thread per pencil: advance the step; at the end of a sweep apply the
 // stopping rule (no big transformation, Section 6.1.7) or C_max, record the
-// sweep's counts, reset the counters.  *active_count = pencils still running.
+// sweep's counts, reset the counters.  ctl[0] = pencils still running,
+// ctl[1] = ticks run.  Inside the solve's graph (loop != 0) the kernel also
+// decides on the device whether the graph's while loop runs another tick:
+// while some pencil is active and fewer than max_ticks ticks have run.
 __global__ void control_batched(const BPencil *__restrict__ P, BState *__restrict__ S, int batch,
                                 int max_sweeps, long long *__restrict__ hist, int hist_len,
-                                int *__restrict__ active_count)
+                                int *__restrict__ ctl, cudaGraphConditionalHandle loop_handle, int loop,
+                                long long max_ticks)
 {
     __shared__ int count;
     if (threadIdx.x == 0) count = 0;
@@ -139,7 +144,12 @@ __global__ void control_batched(const BPencil *__restrict__ P, BState *__restric
         if (st.active) atomicAdd(&count, 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0) *active_count = count;
+    if (threadIdx.x == 0) {
+        ctl[0] = count;
+        const int ticks = ctl[1] + 1;
+        ctl[1] = ticks;
+        if (loop) cudaGraphSetConditional(loop_handle, (count > 0 && ticks < max_ticks) ? 1u : 0u);
+    }
 }
 
 __global__ void state_init(BState *S, int batch)
@@ -298,7 +308,7 @@ static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, con
         BT_TRY(cudaMalloc((void **)&bb.d_hist, sizeof(long long) * 2 * kHistLen * batch));
         bb.cap_batch = batch;
     }
-    if (!bb.d_active) BT_TRY(cudaMalloc((void **)&bb.d_active, sizeof(int)));
+    if (!bb.d_active) BT_TRY(cudaMalloc((void **)&bb.d_active, 2 * sizeof(int)));
     const long long nwork = (long long)pl.gram_work + pl.inner_work + pl.update_work;
     if (nwork > bb.cap_work) {
         cudaFree(bb.d_work);
@@ -416,7 +426,8 @@ static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, con
 }
 
 static cudaError_t enqueue_tick(const BatchBuffers &bb, const Plan &pl, int batch, int inner_sweeps,
-                                int crit_mode, int max_sweeps, cudaStream_t st)
+                                int crit_mode, int max_sweeps, cudaStream_t st,
+                                cudaGraphConditionalHandle loop_handle = 0, int loop = 0, long long max_ticks = 0)
 {
     const int4 *wg = bb.d_work;
     const int4 *wi = wg + pl.gram_work;
@@ -430,7 +441,7 @@ static cudaError_t enqueue_tick(const BatchBuffers &bb, const Plan &pl, int batc
     hz::update_batched<<<pl.update_work, 256, hz::update_smem(sizeof(double2)), st>>>(
         bb.d_pen, bb.d_state, wu);
     hz::control_batched<<<1, 128, 0, st>>>(bb.d_pen, bb.d_state, batch, max_sweeps, bb.d_hist,
-                                           kHistLen, bb.d_active);
+                                           kHistLen, bb.d_active, loop_handle, loop, max_ticks);
     return cudaGetLastError();
 }
 
@@ -443,38 +454,48 @@ static cudaError_t batch_attributes()
                                 (int)hz::update_smem(sizeof(double2)));
 }
 
-// Run ticks until no pencil is active: a graph of `ticks_per_graph` ticks is
-// captured once and replayed.  Returns the number of ticks launched.
+// Run ticks until no pencil is active, as one graph launch: the graph is a
+// conditional while node whose body is one tick (Gram, inner level, update,
+// control); the control kernel sets the loop condition on the device, so the
+// host waits once for the whole solve.  Returns the number of ticks run.
 static ghsvd_status run_ticks(BatchBuffers &bb, const Plan &pl, int batch, const ghsvd_opts &o,
                               cudaStream_t st, long long max_ticks, long long *ticks_out)
 {
-    const int tpg = 8;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cs = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    for (int t = 0; e == cudaSuccess && t < tpg; ++t)
-        e = enqueue_tick(bb, pl, batch, o.inner_sweeps, o.crit_mode, o.max_sweeps, cs);
-    if (e == cudaSuccess) e = cudaStreamEndCapture(cs, &graph);
-    else if (cs) {
-        cudaGraph_t g2 = nullptr;
-        cudaStreamEndCapture(cs, &g2);
-        if (g2) cudaGraphDestroy(g2);
+    cudaGraphConditionalHandle handle = 0;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = handle;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t ec = enqueue_tick(bb, pl, batch, o.inner_sweeps, o.crit_mode, o.max_sweeps, cs, handle, 1,
+                                          max_ticks);
+            cudaGraph_t captured = nullptr;
+            e = cudaStreamEndCapture(cs, &captured);
+            if (e == cudaSuccess) e = ec;
+        }
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    long long ticks = 0;
-    int active = batch;
-    while (e == cudaSuccess && active > 0 && ticks < max_ticks) {
-        e = cudaGraphLaunch(exec, st);
-        ticks += tpg;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&active, bb.d_active, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    }
+    int ctl[2] = {batch, 0};
+    if (e == cudaSuccess) e = cudaMemsetAsync(bb.d_active + 1, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctl, bb.d_active, sizeof(ctl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (cs) cudaStreamDestroy(cs);
-    if (ticks_out) *ticks_out = ticks;
+    if (ticks_out) *ticks_out = ctl[1];
     if (e != cudaSuccess) return GHSVD_ERR_CUDA;
     return GHSVD_OK;
 }
@@ -497,7 +518,8 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
                                                  const void *const *V0, const int64_t *ldv0,
                                                  double *const *lambda, void *const *V,
                                                  const int64_t *ldv, int *sweeps, int *status,
-                                                 int *w_chosen, double *ms_solve, void *stream)
+                                                 int *w_chosen, double *ms_solve, long long *ticks_out,
+                                                 void *stream)
 {
     BatchBuffers &bb = *(BatchBuffers *)buffers;
     const ghsvd_opts &o = *opts;
@@ -559,6 +581,7 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
     long long ticks = 0;
     s = run_ticks(bb, pl, batch, o, st, max_ticks + 16, &ticks);
     if (s != GHSVD_OK) return s;
+    if (ticks_out) *ticks_out = ticks;
     std::vector<BState> hs(batch);
     if (cudaMemcpyAsync(hs.data(), bb.d_state, sizeof(BState) * batch, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return GHSVD_ERR_CUDA;

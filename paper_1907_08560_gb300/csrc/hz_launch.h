@@ -152,6 +152,10 @@ cudaError_t launch_gram_tc(const void *W32, const int8_t *Jrow, const StepArgs &
                            int *err, cudaStream_t s);
 cudaError_t launch_update_tc(void *W32, const StepArgs &a, int n, const double2 *zhat, const int *pair_flag,
                              int *err, int sms, cudaStream_t s);
+// tc_flag[p] = 1: pair p goes to launch_update_tc (its Z^ - I is small);
+// cc_flag[p] = 1: to the FP32 CUDA-core launch_update; both 0: no transformation.
+cudaError_t launch_route(const double2 *zhat, const int *pair_flag, int kk, int npairs, int *tc_flag,
+                         int *cc_flag, cudaStream_t s);
 
 // Phase 2 (hz_urv.cu): the (J, I) URV shortening of Section 5.
 size_t urv_workspace_bytes(long long m, long long p, int n);
@@ -187,4 +191,4 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
                             const void *const *F, const int64_t *ldf, const int8_t *const *J,
                             const int64_t *n_plus, const void *const *G, const int64_t *ldg,
                             const void *const *V0, const int64_t *ldv0, double *const *lambda, void *const *V, const int64_t *ldv, int *sweeps,
-                            int *status, int *w_chosen, double *ms_solve, void *stream);
+                            int *status, int *w_chosen, double *ms_solve, long long *ticks, void *stream);

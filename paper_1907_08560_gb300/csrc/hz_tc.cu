@@ -661,6 +661,46 @@ cudaError_t make_map(CUtensorMap *map, const void *W32, long long ld, int n, int
 
 }  // namespace
 
+// Route each pair of a complex64 step to one of the two updates: the
+// tensor-core update (delta form) when every entry of E = Z^ - I is at most
+// TC_SMALL_E in real and imaginary part, so that its error, about
+// 2^-21 |X||E| with the tensor cores' FP32 accumulation, stays at the FP32
+// rounding of X + X E; the FP32 CUDA-core update otherwise (the large
+// rotations and prescalings of the first sweeps).  Measured on the n = 64
+// and n = 256 test pencils (one complex64 round) and the n = 2048 benchmark
+// pencil: with every pair on the tensor cores the complex64 sweeps left
+// Z'_low less consistent with W32 and the FP64 finishing sweeps took 2-3
+// more sweeps on the small pencils; thresholds 2^-6, 2^-3 and 2^-1 all kept
+// their sweep counts, 2^-1 routing most pairs of the n = 2048 solve to the
+// tensor cores.  tc_flag[p], cc_flag[p] in {0, 1}.
+constexpr float TC_SMALL_E = 0.5f;
+
+__global__ void route_kernel(const float2 *__restrict__ zhat, const int *__restrict__ pair_flag, int kk,
+                             float small_e, int *__restrict__ tc_flag, int *__restrict__ cc_flag)
+{
+    __shared__ int large;
+    const int pair = blockIdx.x;
+    if (threadIdx.x == 0) large = 0;
+    __syncthreads();
+    const bool active = pair_flag[pair] != 0;
+    if (active) {
+        const float2 *zp = zhat + (long long)pair * (KKMAX * KKMAX);
+        bool big = false;
+        for (int e = threadIdx.x; e < kk * kk; e += blockDim.x) {
+            const int l = e % kk, j = e / kk;
+            const float2 z = zp[l + KKMAX * j];
+            const float ex = z.x - (l == j ? 1.0f : 0.0f);
+            big |= fabsf(ex) > small_e || fabsf(z.y) > small_e || !(ex == ex) || !(z.y == z.y);
+        }
+        if (big) large = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc_flag[pair] = active && !large;
+        cc_flag[pair] = active && large;
+    }
+}
+
 bool tc_supported(int kk, int npairs, long long ld)
 {
     // W32's base and column stride must be 16-byte aligned (cudaMalloc'd; ld a
@@ -719,6 +759,13 @@ cudaError_t launch_gram_tc(const void *W32, const int8_t *Jrow, const StepArgs &
     a.chunks_s = s.chunks_s;
     const int grid = s.npairs * (s.chunks_h + s.chunks_s);
     tc::gram_tc_kernel<<<grid, tc::G_THREADS, tc::G_SMEM, st>>>(map, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_route(const double2 *zhat, const int *pair_flag, int kk, int npairs, int *tc_flag, int *cc_flag,
+                         cudaStream_t st)
+{
+    route_kernel<<<npairs, 256, 0, st>>>((const float2 *)zhat, pair_flag, kk, TC_SMALL_E, tc_flag, cc_flag);
     return cudaGetLastError();
 }
 

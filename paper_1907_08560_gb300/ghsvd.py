@@ -54,7 +54,8 @@ class ghsvd_stats(ctypes.Structure):
                 ("launches_update", ctypes.c_longlong), ("ms_gram", ctypes.c_double),
                 ("ms_inner", ctypes.c_double), ("ms_update", ctypes.c_double),
                 ("rounds_low", ctypes.c_int), ("ms_phase2", ctypes.c_double),
-                ("n2x2", ctypes.c_int), ("sweeps_tc", ctypes.c_int)]
+                ("n2x2", ctypes.c_int), ("sweeps_tc", ctypes.c_int),
+                ("batch_ticks", ctypes.c_longlong), ("batch_graph_launches", ctypes.c_int)]
 
 
 class GhsvdError(RuntimeError):
@@ -520,7 +521,8 @@ def ghsvd_get_stats(h) -> dict:
                 launches_inner=st.launches_inner, launches_update=st.launches_update,
                 ms_gram=st.ms_gram, ms_inner=st.ms_inner, ms_update=st.ms_update,
                 rounds_low=st.rounds_low, ms_phase2=st.ms_phase2, n2x2=st.n2x2,
-                sweeps_tc=st.sweeps_tc)
+                sweeps_tc=st.sweeps_tc, batch_ticks=st.batch_ticks,
+                batch_graph_launches=st.batch_graph_launches)
 
 
 def ghsvd_urv(F, J, G, n_plus: int | None = None, stream=None):
