@@ -57,3 +57,26 @@ def eig_tol_vec(F, G, J, ref_lam, ref_F):
     amp = hyperbolic_amp(ref_F, J)
     order = np.argsort(np.asarray(ref_lam))
     return eig_tol(F, G) * amp[order]
+
+
+def fullsize_golden(name):
+    """A case of tests/golden/fullsize_oracle.json (written by
+    tests/golden/make_fullsize.py from the FP64 oracle alone): the oracle's
+    eigenvalues sorted ascending, and the per-eigenvalue FP64 tolerance
+    1e-12 * max(1, (cond(F_c) + cond(G_c)) / 1e3) * a_j in the same order."""
+    import json
+    path = os.path.join(ROOT, "tests", "golden", "fullsize_oracle.json")
+    with open(path) as f:
+        cases = {c["name"]: c for c in json.load(f)["cases"]}
+    c = dict(cases[name])
+    c["lam"] = np.array([float(x) for x in c["lam"]])
+    c["amp"] = np.array([float(x) for x in c["amp"]])
+    c["tol"] = 1e-12 * max(1.0, (c["cond_F_c"] + c["cond_G_c"]) / 1e3) * c["amp"]
+    return c
+
+
+def golden_ratio(lam, golden):
+    """max_j |lam_j - lam_j^oracle| / (|lam_j^oracle| tol_j), both sorted ascending."""
+    ref = golden["lam"]
+    err = np.abs(np.sort(np.asarray(lam, dtype=np.float64)) - ref) / np.abs(ref)
+    return float(np.max(err / golden["tol"]))

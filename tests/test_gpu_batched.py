@@ -61,6 +61,13 @@ def test_batched_equals_single_pencil_solves(gh):
     lams, _, sweeps, statuses, st = s.solve_batched(
         [dev(gh, F) for F, _, _ in batch], [dev(gh, G) for _, _, G in batch],
         [torch.from_numpy(J).cuda() for _, J, _ in batch])
+    # one graph launch; its while loop ran one tick per outer step until the
+    # last pencil stopped (the control kernel ends the loop on the device):
+    # max over the pencils of (steps per sweep) x (sweeps)
+    stt = s.stats()
+    assert stt["batch_graph_launches"] == 1
+    steps = [len(oracle.partition(F.shape[1], 16)) - 2 for F, _, _ in batch]
+    assert stt["batch_ticks"] == max(st_ * sw for st_, sw in zip(steps, sweeps))
     for (F, J, G), lam, sw in zip(batch, lams, sweeps):
         one = gh.Solver(0, block_width=16)
         l1, _, sw1, st1 = one.solve(dev(gh, F), dev(gh, G), torch.from_numpy(J).cuda())
@@ -116,3 +123,22 @@ def test_batched_identity_signature_without_J(gh):
     assert st == gh.GHSVD_OK
     for lam, ref in zip(lams, lams_ref):
         assert rel_err(lam.cpu().numpy(), ref).max() < 1e-12
+
+
+def test_batched_kpoint_pencils_match_oracle_golden(gh):
+    # three of the 64 k-point pencils of the batched workload (n = 1511, 1147,
+    # 1272; F 1.5n x n with 20 % negative signs, G 2n x n, cond(S) up to 6e9),
+    # solved together with the autotuned block width, against the FP64
+    # oracle's eigenvalues stored by tests/golden/make_fullsize.py
+    from conftest import fullsize_golden, golden_ratio
+    names = ("kpt56", "kpt11", "kpt23")
+    goldens = [fullsize_golden(nm) for nm in names]
+    pens = [P.batch_pencil(g["n"], g["cond_s"], g["seed"]) for g in goldens]
+    s = gh.Solver(0, block_width=0, max_sweeps=80)
+    lams, Vs, sweeps, statuses, st = s.solve_batched(
+        [dev(gh, F) for F, _, _ in pens], [dev(gh, G) for _, _, G in pens],
+        [torch.from_numpy(J).cuda() for _, J, _ in pens], want_vectors=False)
+    s.close()
+    assert st == gh.GHSVD_OK and all(x == 0 for x in statuses)
+    for g, lam in zip(goldens, lams):
+        assert golden_ratio(lam.cpu().numpy(), g) < 1.0, g["name"]

@@ -1,19 +1,23 @@
 """Checks at the benchmark's full size: the n = 2048 LAPW-shaped pencil
 (F 3072 x 2048 with 512 negative signs, G 4096 x 2048, cond(S) = 1e10) in the
-benchmark's configuration (block width 32, C_max 80).  The oracle does not
-finish an n = 2048 solve in test time, so these are properties that hold at
-any size: the definition of the outputs (eq. 3.2: V^* S V = I, V^* H V
-diagonal, computed through the factors, never through S), Sylvester's
-inertia, and the agreement of the mixed-precision and Phase 2 solves with the
-FP64 one within the per-eigenvalue tolerance (reading 12 of the design notes:
-1e-12 * max(1, (cond(F_c) + cond(G_c)) / 1e3) * a_j, cond(F_c) = 1e6 and
-cond(G_c) = 10^5 by construction)."""
+benchmark's configuration (block width 32, C_max 80).
+
+The eigenvalues of every solve (FP64, mixed precision with FP64 or FP32 2x2
+parameters, Phase 2 first) are compared element by element with the FP64
+oracle's, stored in tests/golden/fullsize_oracle.json by
+tests/golden/make_fullsize.py (a whole blocked oracle solve on the CPU), within
+the per-eigenvalue tolerance 1e-12 * max(1, (cond(F_c) + cond(G_c)) / 1e3) * a_j
+(eq. 3.2; a_j the hyperbolic amplification of the oracle's converged column j).
+Beside that, properties that hold at any size: the definition of the outputs
+(eq. 3.2: V^* S V = I, V^* H V diagonal, computed through the factors, never
+through S) and Sylvester's inertia."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
 from synth import pencils as P
+from conftest import fullsize_golden, golden_ratio
 
 pytestmark = pytest.mark.gpu
 
@@ -70,12 +74,18 @@ def test_fullsize_inertia(fp64):
     assert int((ev < 0).sum()) == int((fp64["lam"] < 0).sum())
 
 
-@pytest.mark.parametrize("kind", ["mixed", "shortened"])
-def test_fullsize_variants_match_fp64(fp64, kind):
+def test_fullsize_fp64_matches_oracle(fp64):
+    g = fullsize_golden("lapw2048")
+    assert golden_ratio(fp64["lam"].cpu().numpy(), g) < 1.0
+
+
+@pytest.mark.parametrize("kind", ["mixed", "mixed_param32", "shortened"])
+def test_fullsize_variants_match_oracle_and_fp64(fp64, kind):
     gh = fp64["gh"]
     opts = dict(block_width=32, max_sweeps=80)
-    if kind == "mixed":
-        opts.update(precision=gh.GHSVD_PRECISION_MIXED, mixed_max_sweeps=60)
+    if kind.startswith("mixed"):
+        opts.update(precision=gh.GHSVD_PRECISION_MIXED, mixed_max_sweeps=60,
+                    mixed_param32=int(kind == "mixed_param32"))
     else:
         opts.update(shorten=1)
     s = gh.Solver(0, **opts)
@@ -88,3 +98,4 @@ def test_fullsize_variants_match_fp64(fp64, kind):
     tol = 1e-12 * max(1.0, (1e6 + 1e5) / 1e3) * fp64["amp"][order]
     err = np.abs(np.sort(lam.cpu().numpy()) - ref[order]) / np.abs(ref[order])
     assert np.all(err < tol), (err / tol).max()
+    assert golden_ratio(lam.cpu().numpy(), fullsize_golden("lapw2048")) < 1.0
