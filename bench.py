@@ -212,6 +212,23 @@ def run_batched(args):
         tol = 1e-12 * max(1.0, (1e6 + 1e5) / 1e3) * amp[o]
         err = np.abs(np.sort(lam.cpu().numpy()) - l1[o]) / np.abs(l1[o])
         worst = max(worst, float((err / tol).max()))
+    # the pencils of this batch whose FP64 oracle eigenvalues are stored
+    # (tests/golden/fullsize_oracle.json, written by tests/golden/make_fullsize.py)
+    golden = {}
+    gpath = os.path.join(ROOT, "tests", "golden", "fullsize_oracle.json")
+    if (args.batch, args.batch_lo, args.batch_hi) == (64, 256, 1536) and os.path.exists(gpath):
+        with open(gpath) as f:
+            for c in json.load(f)["cases"]:
+                i = c.get("batch_index")
+                if c.get("generator") != "batch_pencil" or i is None or i >= len(batch):
+                    continue
+                ref = np.array([float(x) for x in c["lam"]])
+                tol = 1e-12 * max(1.0, (c["cond_F_c"] + c["cond_G_c"]) / 1e3) * \
+                    np.array([float(x) for x in c["amp"]])
+                err = np.abs(np.sort(lams[i].cpu().numpy()) - ref) / np.abs(ref)
+                golden[c["name"]] = {"n": c["n"], "eig_rel_err_over_tol_max": float((err / tol).max()),
+                                     "oracle_sweeps": c["sweeps"], "gpu_sweeps": int(sweeps[i])}
+    bst = solver.stats()
     ns = [F.shape[1] for F, _, _ in batch]
     line = {"metric": f"HZ GHSVD batched solves/s ({len(batch)} k-point pencils, n in "
                       f"[{args.batch_lo},{args.batch_hi}])",
@@ -225,7 +242,12 @@ def run_batched(args):
                        "statuses": sorted(set(statuses))},
             "sequential": {"value": len(batch) / t_seq, "unit": "solves/s", "seconds": t_seq},
             "speedup_vs_sequential": t_seq / t_batch,
-            "eig_rel_diff_vs_sequential_over_tol_max": worst, "clocks": clk}
+            "eig_rel_diff_vs_sequential_over_tol_max": worst,
+            "vs_fp64_oracle": golden,
+            "graph": {"launches": bst["batch_graph_launches"], "ticks": bst["batch_ticks"],
+                      "what": "one CUDA graph launch per batched solve; a conditional while node "
+                              "repeats the tick, the control kernel ends it on the device"},
+            "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -350,15 +372,14 @@ def run_warmstart(args):
     t0 = time.perf_counter()
     _, Vs, sw_train, st_train, _ = ws.solve_many(solver, fam, train_t,
                                                  V0s=ws.reference_v0(fam, Vref, train_t))
-    T = ws.canonical_targets(Vs, Vref)
+    T, scale = ws.canonical_targets(Vs, Vref)         # normalized targets and their scale
     del Vs
     t_data = time.perf_counter() - t0
-    scale = float(T.std())
     net = ghsvd.Mlp(4, 64, T.shape[1], seed=3)
     X = torch.as_tensor(train_t, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    loss = net.train(X, T / scale, epochs=args.epochs, batch=100, lr=1e-3)
+    loss = net.train(X, T, epochs=args.epochs, batch=100, lr=1e-3)
     t_train = time.perf_counter() - t0
     del T
     # held-out solves: warm up once on a small subset, then time each start
@@ -369,14 +390,16 @@ def run_warmstart(args):
     V0r = ws.reference_v0(fam, Vref, test_t)
     torch.cuda.synchronize()
     t_ref_prep = time.perf_counter() - t0
-    refr = ws.solve_many(solver, fam, test_t, V0s=V0r)
+    tr = {}
+    refr = ws.solve_many(solver, fam, test_t, V0s=V0r, times=tr)
     del V0r
     torch.cuda.synchronize()
+    tl = {}
     t0 = time.perf_counter()
-    V0l = ws.predict_v0(net, fam, Vref, test_t, scale)
+    V0l = ws.predict_v0(net, fam, Vref, test_t, scale, times=tl)
     torch.cuda.synchronize()
     t_pred = time.perf_counter() - t0
-    learned = ws.solve_many(solver, fam, test_t, V0s=V0l)
+    learned = ws.solve_many(solver, fam, test_t, V0s=V0l, times=tl)
     del V0l
     # equal error: on a sample of the held-out pencils, the eigenvalues of the
     # cold and of the learned-start solves against the FP64 CPU oracle, per
@@ -420,6 +443,14 @@ def run_warmstart(args):
             "solves_per_s": {"cold_V0_I": n_test / t_cold, "V0_reference_V_t0": n_test / t_ref,
                              "V0_learned": n_test / t_learn},
             "speedup_vs_cold": t_cold / t_learn, "speedup_vs_reference_start": t_ref / t_learn,
+            "learned_seconds": {"mlp_forward_and_compose": tl.get("predict_s"),
+                                "s_orthonormalize": tl.get("s_orthonormalize_s"),
+                                "prediction_total": t_pred,
+                                "apply_v0_in_solve": tl.get("v0_apply_s"),
+                                "solve_total": learned[4], "cold_solve_total": t_cold},
+            "reference_start_seconds": {"s_orthonormalize": t_ref_prep,
+                                        "apply_v0_in_solve": tr.get("v0_apply_s"),
+                                        "solve_total": refr[4]},
             "statuses": sorted(set(cold[3] + refr[3] + learned[3])),
             "eig_err_vs_oracle_over_tol_max": worst, "oracle_sample": len(sample)}
     print(json.dumps(line), flush=True)
@@ -515,7 +546,7 @@ def main():
     torch.cuda.synchronize()
 
     acc = dict(ms_update=0.0, launches_update=0, ms_gram=0.0, launches_gram=0, ms_inner=0.0,
-               launches_inner=0, kernel_launches=0, sweeps=0)
+               launches_inner=0, kernel_launches=0, sweeps=0, pairs_delta=0, pairs_fp64=0)
     clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
@@ -557,6 +588,11 @@ def main():
                 "executed_frac": 0.75 * achieved / peak_tflops if peak_tflops else None,
                 "traffic": traffic_per_launch() if N == 2048 else None,
                 "kernel": "update_kernel<double,double>",
+                "update_phase": ("the update phase of a step: the FP64 product (update_kernel) for "
+                                 "pairs with a large transformation, the delta form "
+                                 "(update_delta64_kernel) for pairs whose Z^ - I <= 2^-29, and the "
+                                 "routing kernel; timed together with CUDA events"),
+                "pairs_delta_form": acc["pairs_delta"], "pairs_fp64_product": acc["pairs_fp64"],
                 "peak_source": "FP64 DFMA measured live on this GPU (libhzpeak)",
                 "gram": {"achieved": gram_flops_per_launch(**sizes) / (gram_ms * 1e-3) / 1e12,
                          "ms_per_launch": gram_ms},

@@ -130,6 +130,13 @@ typedef struct {
                             cores.  0: Grams and updates on the CUDA cores.
                             The 2x2 parameters, J-norms and stopping test are
                             FP64 either way.                                  */
+    int delta_update;    /* FP64 sweeps: 1 (default) updates every pair whose
+                            Z^ - I has all entries <= 2^-29 in the delta form
+                            X + X (Z^ - I), the product from FP32 roundings by
+                            FP32 FMAs, the sum in FP64 (as accurate as the FP64
+                            product: its error stays below 2^-53 |X|); the
+                            other pairs, and every pair with 0, by the FP64
+                            product                                           */
 } ghsvd_opts;
 
 /* Per-solve statistics (Section 6.4.3, "Completing a sweep"). */
@@ -153,6 +160,12 @@ typedef struct {
                                       of every active pencil) run on the device  */
     int batch_graph_launches;      /* ghsvd_solve_batched: launches of the solve's
                                       graph (its while loop runs on the device)  */
+    double ms_v0;                  /* warm starts: wall time of applying the
+                                      starting bases, (F V0, G V0), ms         */
+    long long pairs_delta;         /* with opts.delta_update: FP64 pair updates
+                                      taken in the delta form, over the solve  */
+    long long pairs_fp64;          /* with opts.delta_update: FP64 pair updates
+                                      by the FP64 product, over the solve      */
 } ghsvd_stats;
 
 /* Fill *opts with the defaults listed above. */
@@ -316,6 +329,23 @@ ghsvd_status ghsvd_mlp_train(ghsvd_mlp_t m, int n_samples, const float *X, const
 ghsvd_status ghsvd_s_orthonormalize(int count, int64_t p, int64_t n, const void *const *G,
                                     const int64_t *ldg, void *const *V0, const int64_t *ldv0,
                                     void *stream);
+
+/* The MLP's training targets from the solver's eigenvectors V_i (device,
+ * complex128 n x n column-major, phases aligned with Vref by
+ * ghsvd_align_phases, columns in ascending eigenvalue order): row i of T
+ * (device FP32, count x 2 n^2, row-major) = vec(V_i - Vref) as (re, im)
+ * pairs in column-major order, divided by their root mean square over all
+ * rows, which is returned in *rms (host, may be NULL). */
+ghsvd_status ghsvd_v0_targets(int count, int64_t n, const void *Vref, int64_t ldr, const void *const *V,
+                              const int64_t *ldv, float *T, double *rms, void *stream);
+
+/* The predicted starting bases: V0_i = Vref + scale D_i, D_i the complex n x n
+ * matrix (column-major (re, im) pairs) in row i of Y (device FP32,
+ * count x 2 n^2, row-major: the MLP's output for parameter vector i); V0 is
+ * a host array of `count` device pointers (complex128, leading dimensions
+ * ldv0).  Follow with ghsvd_s_orthonormalize. */
+ghsvd_status ghsvd_v0_compose(int count, int64_t n, const float *Y, double scale, const void *Vref, int64_t ldr,
+                              void *const *V0, const int64_t *ldv0, void *stream);
 
 /* V[:, j] *= conj(c_j)/|c_j|, c_j = Vref[:, j]^* V[:, j] (device, complex128,
  * n x n column-major): aligns the free phase of each eigenvector with a

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libghsvd.so")
 PEAK_LIB = os.path.join(HERE, "libhzpeak.so")
 SOURCES = ["ghsvd_api.cu", "hz_step.cu", "ghsvd_noalloc.cu", "hz_batch.cu", "hz_warm.cu",
-           "hz_urv.cu", "hz_phase4.cu", "hz_tc.cu"]
+           "hz_urv.cu", "hz_phase4.cu", "hz_tc.cu", "hz_delta.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

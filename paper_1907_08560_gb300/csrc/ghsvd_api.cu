@@ -184,6 +184,7 @@ ghsvd_status ghsvd_default_opts(ghsvd_opts *o)
     o->timeout_ms = 0;
     o->shorten = 0;
     o->mixed_tc = 1;
+    o->delta_update = 1;
     return GHSVD_OK;
 }
 
@@ -218,7 +219,7 @@ ghsvd_status ghsvd_create(ghsvd_t *out, int device, const ghsvd_opts *opts)
         (o.precision != GHSVD_PRECISION_FP64 && o.precision != GHSVD_PRECISION_MIXED) ||
         o.mixed_max_sweeps < 0 || o.gram_chunk < 0 || (o.timing != 0 && o.timing != 1) ||
         (o.shorten != 0 && o.shorten != 1) || o.ordering != GHSVD_ORDER_ROUND_ROBIN ||
-        (o.mixed_param32 != 0 && o.mixed_param32 != 1) || (o.mixed_tc != 0 && o.mixed_tc != 1) ||
+        (o.mixed_param32 != 0 && o.mixed_param32 != 1) || (o.mixed_tc != 0 && o.mixed_tc != 1) || (o.delta_update != 0 && o.delta_update != 1) ||
         !(o.tol_scale > 0.0 && o.tol_scale < 1e300) || o.timeout_ms < 0)
         return GHSVD_ERR_INVALID_ARG;
     int ndev = 0;
@@ -235,7 +236,7 @@ ghsvd_status ghsvd_create(ghsvd_t *out, int device, const ghsvd_opts *opts)
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = hz::setup_kernels();
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_counters, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_counters, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_err, 2 * sizeof(int));
     cudaSetDevice(prev);
     if (e != cudaSuccess) {
@@ -350,7 +351,9 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
         h->cap_n = n;
     }
     if (!h->counters) {
-        CUDA_TRY(cudaMalloc((void **)&h->counters, 2 * sizeof(unsigned long long)));
+        // all, big transformations of the sweep; FP64 pair updates in the
+        // delta form and by the FP64 product
+        CUDA_TRY(cudaMalloc((void **)&h->counters, 4 * sizeof(unsigned long long)));
         CUDA_TRY(cudaMalloc((void **)&h->err, 2 * sizeof(int)));
         CUDA_TRY(cudaMalloc((void **)&h->kappa, sizeof(double)));
     }
@@ -372,6 +375,7 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
     }
 
     // inputs: J (host or device) -> padded signs; [F; G; V0 or I] -> W
+    auto t_v0 = std::chrono::steady_clock::now();
     CUDA_TRY(cudaMemsetAsync(h->err, 0, 2 * sizeof(int), st));
     const int8_t *Jd = nullptr;
     if (J) {
@@ -400,15 +404,24 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
         CUDA_TRY(hz::launch_v0_kappa(h->d_item, 1, d_kap, st));
         CUDA_TRY(cudaMemcpyAsync(&kap, d_kap, 8, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
-        const hz::GemmItem item{h->W, Mt, Mt, (const double2 *)V0, ldv0, h->Wtmp, Mt, n,
+        t_v0 = std::chrono::steady_clock::now();
+        // the rows of F and G only: the rows of Z' (= I) become V0 itself
+        const long long fg = (long long)m_pad + p_pad;
+        const hz::GemmItem item{h->W, Mt, fg, (const double2 *)V0, ldv0, h->Wtmp, Mt, n,
                                 !(kap <= hz::WARM_ACCURATE_KAPPA)};
         CUDA_TRY(cudaMemcpyAsync(h->d_item, &item, sizeof(item), cudaMemcpyHostToDevice, st));
-        CUDA_TRY(hz::launch_gemm_batched(h->d_item, 1, Mt, n, st));
+        CUDA_TRY(hz::launch_gemm_batched(h->d_item, 1, fg, n, st));
         h->stats.kernel_launches += 1;
-        CUDA_TRY(cudaMemcpyAsync(h->W, h->Wtmp, sizeof(double2) * Mt * n, cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(cudaMemcpy2DAsync(h->W, sizeof(double2) * Mt, h->Wtmp, sizeof(double2) * Mt,
+                                   sizeof(double2) * fg, n, cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(cudaMemcpy2DAsync(h->W + fg, sizeof(double2) * Mt, V0, sizeof(double2) * ldv0,
+                                   sizeof(double2) * n, n, cudaMemcpyDeviceToDevice, st));
     }
     CUDA_TRY(cudaMemcpyAsync(h->h_err, h->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    if (V0)
+        h->stats.ms_v0 =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_v0).count();
     if (h->h_err[1]) return GHSVD_ERR_INVALID_ARG;
     if (h->h_err[0] & hz::DEVERR_NONFINITE) return GHSVD_ERR_NONFINITE;
 
@@ -470,8 +483,9 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
             ia.tol = single ? tol32 : tol64;
             ia.cpp = tcs ? chunks_h_tc + chunks_s_tc : chunks_h + chunks_s;
             ia.chunks_h = tcs ? chunks_h_tc : chunks_h;
-            CUDA_TRY(cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned long long), st));
+            CUDA_TRY(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned long long), st));
             const bool timed = o.timing != 0;
+            const bool delta = !single && o.delta_update;
             if (timed) CUDA_TRY(h->timer.reserve(6 * nsteps));
             cudaEvent_t *ev = timed ? h->timer.ev.data() : nullptr;
             for (int r = 0; r < nsteps; ++r) {
@@ -497,6 +511,13 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
                     CUDA_TRY(hz::launch_route(h->zhat, h->pair_flag, kk, npairs, tcf, ccf, st));
                     CUDA_TRY(hz::launch_update_tc(Wc, sa, n, h->zhat, tcf, h->err, h->num_sms, st));
                     CUDA_TRY(hz::launch_update(Wc, true, sa, h->zhat, ccf, st));
+                } else if (delta) {
+                    // pairs whose Z^ - I is tiny in the delta form (hz_delta.cu),
+                    // the others by the FP64 product
+                    int *df = h->route, *ff = h->route + npairs;
+                    CUDA_TRY(hz::launch_route64(h->zhat, h->pair_flag, kk, npairs, df, ff, h->counters + 2, st));
+                    CUDA_TRY(hz::launch_update_delta64(h->W, sa, h->zhat, df, st));
+                    CUDA_TRY(hz::launch_update(Wc, false, sa, h->zhat, ff, st));
                 } else {
                     CUDA_TRY(hz::launch_update(Wc, single, sa, h->zhat, h->pair_flag, st));
                 }
@@ -505,8 +526,8 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
             h->stats.launches_gram += nsteps;
             h->stats.launches_inner += nsteps;
             h->stats.launches_update += nsteps;
-            h->stats.kernel_launches += (tcs ? 5LL : 3LL) * nsteps;
-            CUDA_TRY(cudaMemcpyAsync(h->h_counters, h->counters, 2 * sizeof(unsigned long long),
+            h->stats.kernel_launches += (tcs || delta ? 5LL : 3LL) * nsteps;
+            CUDA_TRY(cudaMemcpyAsync(h->h_counters, h->counters, 4 * sizeof(unsigned long long),
                                      cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaMemcpyAsync(h->h_err, h->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaStreamSynchronize(st));
@@ -528,6 +549,10 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
             ++sweeps;
             if (single) ++sweeps_low;
             if (tcs) ++h->stats.sweeps_tc;
+            if (delta) {
+                h->stats.pairs_delta += (long long)h->h_counters[2];
+                h->stats.pairs_fp64 += (long long)h->h_counters[3];
+            }
             if (h->h_err[0] & hz::DEVERR_TIMEOUT) { status = GHSVD_ERR_CUDA; break; }
             if (h->h_err[0] & hz::DEVERR_RANK) { status = GHSVD_ERR_RANK_DEFICIENT; break; }
             if (h->h_err[0] & hz::DEVERR_NONFINITE) { status = GHSVD_ERR_NONFINITE; break; }
@@ -789,8 +814,11 @@ extern "C" ghsvd_status ghsvd_solve_batched(ghsvd_t h, int batch, const int64_t 
     int w = 0;
     double ms = 0;
     long long ticks = 0;
+    double ms_v0 = 0.0;
     ghsvd_status s = hz_batch_solve(h->batch, h->device, &h->opts, batch, m, p, n, F, ldf, J, n_plus,
-                                    G, ldg, V0, ldv0, lambda, V, ldv, sweeps, status, &w, &ms, &ticks, stream);
+                                    G, ldg, V0, ldv0, lambda, V, ldv, sweeps, status, &w, &ms, &ticks, &ms_v0,
+                                    stream);
+    h->stats.ms_v0 = ms_v0;
     h->stats.block_width = w;
     h->stats.ms_total = ms;
     h->stats.batch_ticks = ticks;

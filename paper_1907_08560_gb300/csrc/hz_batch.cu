@@ -23,7 +23,9 @@
 #include <vector>
 
 #include "../../include/ghsvd.h"
-#include "hz_kernels.cuh"
+#include "hz_gram.cuh"
+#include "hz_inner.cuh"
+#include "hz_update.cuh"
 #include "hz_launch.h"
 
 namespace hz {
@@ -247,7 +249,7 @@ Plan make_plan(int batch, const int64_t *m, const int64_t *p, const int64_t *n, 
         pl.pp.push_back(q);
     }
     pl.oItems = pl.bytes;
-    pl.bytes += a256((long long)sizeof(hz::GemmItem) * batch);
+    pl.bytes += a256((long long)sizeof(hz::GemmItem) * 2 * batch);   // products, then two copies each
     pl.oKap0 = pl.bytes;
     pl.bytes += a256(8LL * batch);
     return pl;
@@ -291,7 +293,8 @@ constexpr int kHistLen = 64;
 static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, const void *const *F,
                                 const int64_t *ldf, const int8_t *const *J, const int64_t *n_plus,
                                 const void *const *G, const int64_t *ldg, const void *const *V0,
-                                const int64_t *ldv0, cudaStream_t st, double tol_scale)
+                                const int64_t *ldv0, cudaStream_t st, double tol_scale,
+                                double *ms_v0 = nullptr)
 {
     if (pl.bytes > bb.arena_bytes) {
         cudaFree(bb.arena);
@@ -389,18 +392,26 @@ static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, con
             double2 *Wi = (double2 *)(bb.arena + q.oW);
             double2 *Ti = (double2 *)(bb.arena + q.oTmp);
             const int acc = !(kap[kidx++] <= hz::WARM_ACCURATE_KAPPA);
-            items.push_back({Wi, q.Mt, q.Mt, (const double2 *)V0[i], ldv0[i], Ti, q.Mt, q.n, acc});
-            back.push_back({Ti, q.Mt, q.Mt, nullptr, 0, Wi, q.Mt, q.n, 0});
-            max_rows = std::max(max_rows, q.Mt);
+            // the rows of F and G only; the rows of Z' (= I) become V0 itself
+            const long long fg = (long long)q.m_pad + q.p_pad;
+            items.push_back({Wi, q.Mt, fg, (const double2 *)V0[i], ldv0[i], Ti, q.Mt, q.n, acc});
+            back.push_back({Ti, q.Mt, fg, nullptr, 0, Wi, q.Mt, q.n, 0});
+            back.push_back({(const double2 *)V0[i], ldv0[i], q.n, nullptr, 0, Wi + fg, q.Mt, q.n, 0});
+            max_rows = std::max(max_rows, fg);
             max_n = std::max(max_n, q.n);
         }
         if (!items.empty()) {
+            auto tv = std::chrono::steady_clock::now();
             BT_TRY(cudaMemcpyAsync(d_items, items.data(), sizeof(hz::GemmItem) * items.size(),
                                    cudaMemcpyHostToDevice, st));
             BT_TRY(hz::launch_gemm_batched(d_items, (int)items.size(), max_rows, max_n, st));
             BT_TRY(cudaMemcpyAsync(d_items, back.data(), sizeof(hz::GemmItem) * back.size(),
                                    cudaMemcpyHostToDevice, st));
             BT_TRY(hz::launch_copy_batched(d_items, (int)back.size(), st));
+            if (ms_v0) {
+                BT_TRY(cudaStreamSynchronize(st));
+                *ms_v0 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tv).count();
+            }
         }
     }
     for (int i = 0; i < batch; ++i) {
@@ -519,7 +530,7 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
                                                  double *const *lambda, void *const *V,
                                                  const int64_t *ldv, int *sweeps, int *status,
                                                  int *w_chosen, double *ms_solve, long long *ticks_out,
-                                                 void *stream)
+                                                 double *ms_v0, void *stream)
 {
     BatchBuffers &bb = *(BatchBuffers *)buffers;
     const ghsvd_opts &o = *opts;
@@ -564,7 +575,7 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
     if (w_chosen) *w_chosen = w;
     Plan pl = make_plan(batch, m, p, n, w, sms, V0 != nullptr);
     auto t0 = std::chrono::steady_clock::now();
-    ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, V0, ldv0, st, opts->tol_scale);
+    ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, V0, ldv0, st, opts->tol_scale, ms_v0);
     if (s != GHSVD_OK) return s;
     // bad J entries or non-finite inputs
     std::vector<int> herr(2 * batch, 0);

@@ -157,6 +157,15 @@ cudaError_t launch_update_tc(void *W32, const StepArgs &a, int n, const double2 
 cudaError_t launch_route(const double2 *zhat, const int *pair_flag, int kk, int npairs, int *tc_flag,
                          int *cc_flag, cudaStream_t s);
 
+// FP64 sweeps: the delta-form update of pairs whose Z^ - I is tiny
+// (hz_delta.cu).  delta_flag[p] = 1: pair p goes to launch_update_delta64;
+// full_flag[p] = 1: to launch_update (FP64 product); *count += delta pairs.
+cudaError_t delta64_setup();
+cudaError_t launch_route64(const double2 *zhat, const int *pair_flag, int kk, int npairs, int *delta_flag,
+                           int *full_flag, unsigned long long *count, cudaStream_t s);
+cudaError_t launch_update_delta64(double2 *W, const StepArgs &a, const double2 *zhat, const int *delta_flag,
+                                  cudaStream_t s);
+
 // Phase 2 (hz_urv.cu): the (J, I) URV shortening of Section 5.
 size_t urv_workspace_bytes(long long m, long long p, int n);
 cudaError_t launch_urv(int m, int p, int n, const double2 *F, long long ldf, const int8_t *J,
@@ -191,4 +200,5 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
                             const void *const *F, const int64_t *ldf, const int8_t *const *J,
                             const int64_t *n_plus, const void *const *G, const int64_t *ldg,
                             const void *const *V0, const int64_t *ldv0, double *const *lambda, void *const *V, const int64_t *ldv, int *sweeps,
-                            int *status, int *w_chosen, double *ms_solve, long long *ticks, void *stream);
+                            int *status, int *w_chosen, double *ms_solve, long long *ticks, double *ms_v0,
+                            void *stream);

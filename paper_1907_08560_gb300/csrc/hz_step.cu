@@ -5,7 +5,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 
-#include "hz_kernels.cuh"
+#include "hz_gram.cuh"
+#include "hz_inner.cuh"
+#include "hz_update.cuh"
 #include "hz_launch.h"
 
 namespace hz {
@@ -551,6 +553,8 @@ cudaError_t setup_kernels()
                              (int)update_smem(sizeof(float2)));
     if (e != cudaSuccess) return e;
     e = tc_setup();
+    if (e != cudaSuccess) return e;
+    e = delta64_setup();
     if (e != cudaSuccess) return e;
     if (g_cluster_mask < 0) {
         int m64 = 0, m32 = 0;

@@ -445,6 +445,65 @@ cudaError_t mlp_loss_grad(ghsvd_mlp *m, int B, const float *X, const float *T, d
     return cudaGetLastError();
 }
 
+// T_i = vec(V_i - Vref) as FP32 (re, im) pairs, column-major (the MLP's
+// training targets), and the sum of their squares (FP64, one atomic per CTA).
+__global__ void __launch_bounds__(256)
+v0_targets_kernel(const double2 *__restrict__ Vref, long long ldr, const double2 *const *__restrict__ V,
+                  const long long *__restrict__ ldv, int n, float *__restrict__ T, double *__restrict__ sumsq)
+{
+    __shared__ double red[8];
+    const int i = blockIdx.y;
+    const long long nn = (long long)n * n;
+    const double2 *Vi = V[i];
+    const long long lv = ldv[i];
+    double acc = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e % n), c = (int)(e / n);
+        const double2 v = Vi[r + lv * c], w = Vref[r + ldr * c];
+        const float dx = (float)(v.x - w.x), dy = (float)(v.y - w.y);
+        T[(long long)i * 2 * nn + 2 * e] = dx;
+        T[(long long)i * 2 * nn + 2 * e + 1] = dy;
+        acc += (double)dx * dx + (double)dy * dy;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < 8; ++k) s += red[k];
+        atomicAdd(sumsq, s);
+    }
+}
+
+__global__ void scale_f32(float *__restrict__ x, long long count, const double *__restrict__ sumsq, long long total)
+{
+    const double rms = sqrt(*sumsq / (double)total);
+    const float f = rms > 0.0 ? (float)(1.0 / rms) : 1.0f;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+         e += (long long)gridDim.x * blockDim.x)
+        x[e] *= f;
+}
+
+// V0_i = Vref + scale * D_i, D_i the FP32 (re, im) pairs of row i of Y
+// (column-major n x n, the layout of the training targets).
+__global__ void __launch_bounds__(256)
+v0_compose_kernel(const float *__restrict__ Y, double scale, const double2 *__restrict__ Vref, long long ldr,
+                  double2 *const *__restrict__ V0, const long long *__restrict__ ldv0, int n)
+{
+    const int i = blockIdx.y;
+    const long long nn = (long long)n * n;
+    double2 *Vi = V0[i];
+    const long long lv = ldv0[i];
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e % n), c = (int)(e / n);
+        const double2 w = Vref[r + ldr * c];
+        const float dx = Y[(long long)i * 2 * nn + 2 * e], dy = Y[(long long)i * 2 * nn + 2 * e + 1];
+        Vi[r + lv * c] = make_double2(w.x + scale * dx, w.y + scale * dy);
+    }
+}
+
 ghsvd_status st_of(cudaError_t e)
 {
     if (e == cudaSuccess) return GHSVD_OK;
@@ -646,6 +705,67 @@ ghsvd_status ghsvd_s_orthonormalize(int count, int64_t p, int64_t n, const void 
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return st_of(e);
     return hbad ? GHSVD_ERR_RANK_DEFICIENT : GHSVD_OK;
+}
+
+ghsvd_status ghsvd_v0_targets(int count, int64_t n, const void *Vref, int64_t ldr, const void *const *V,
+                              const int64_t *ldv, float *T, double *rms, void *stream)
+{
+    if (count < 1 || n < 1 || n > 4096 || !Vref || ldr < n || !V || !ldv || !T) return GHSVD_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!V[i] || ldv[i] < n) return GHSVD_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double2 **dV = nullptr;
+    long long *dl = nullptr;
+    double *sumsq = nullptr;
+    std::vector<long long> lv(ldv, ldv + count);
+    cudaError_t e = cudaMallocAsync((void **)&dV, sizeof(void *) * count, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dl, sizeof(long long) * count, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&sumsq, sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dV, V, sizeof(void *) * count, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dl, lv.data(), sizeof(long long) * count, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sumsq, 0, sizeof(double), st);
+    const long long nn = n * n, total = 2LL * nn * count;
+    if (e == cudaSuccess) {
+        dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 1024), (unsigned)count);
+        v0_targets_kernel<<<grid, 256, 0, st>>>((const double2 *)Vref, ldr, dV, dl, (int)n, T, sumsq);
+        scale_f32<<<1024, 256, 0, st>>>(T, total, sumsq, total);
+        e = cudaGetLastError();
+    }
+    double hs = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, sumsq, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(dV, st);
+    cudaFreeAsync(dl, st);
+    cudaFreeAsync(sumsq, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (rms) *rms = sqrt(hs / (double)total);
+    return st_of(e);
+}
+
+ghsvd_status ghsvd_v0_compose(int count, int64_t n, const float *Y, double scale, const void *Vref, int64_t ldr,
+                              void *const *V0, const int64_t *ldv0, void *stream)
+{
+    if (count < 1 || n < 1 || n > 4096 || !Y || !Vref || ldr < n || !V0 || !ldv0) return GHSVD_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!V0[i] || ldv0[i] < n) return GHSVD_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    double2 **dV = nullptr;
+    long long *dl = nullptr;
+    std::vector<long long> lv(ldv0, ldv0 + count);
+    cudaError_t e = cudaMallocAsync((void **)&dV, sizeof(void *) * count, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dl, sizeof(long long) * count, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dV, V0, sizeof(void *) * count, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dl, lv.data(), sizeof(long long) * count, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        const long long nn = n * n;
+        dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 1024), (unsigned)count);
+        v0_compose_kernel<<<grid, 256, 0, st>>>(Y, scale, (const double2 *)Vref, ldr, dV, dl, (int)n);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(dV, st);
+    cudaFreeAsync(dl, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return st_of(e);
 }
 
 ghsvd_status ghsvd_align_phases(int64_t n, const void *Vref, int64_t ldr, void *V, int64_t ldv,

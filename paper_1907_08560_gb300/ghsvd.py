@@ -41,7 +41,7 @@ class ghsvd_opts(ctypes.Structure):
                 ("timing", ctypes.c_int), ("ordering", ctypes.c_int),
                 ("tol_scale", ctypes.c_double), ("timeout_ms", ctypes.c_int64),
                 ("mixed_param32", ctypes.c_int), ("shorten", ctypes.c_int),
-                ("mixed_tc", ctypes.c_int)]
+                ("mixed_tc", ctypes.c_int), ("delta_update", ctypes.c_int)]
 
 
 class ghsvd_stats(ctypes.Structure):
@@ -55,7 +55,9 @@ class ghsvd_stats(ctypes.Structure):
                 ("ms_inner", ctypes.c_double), ("ms_update", ctypes.c_double),
                 ("rounds_low", ctypes.c_int), ("ms_phase2", ctypes.c_double),
                 ("n2x2", ctypes.c_int), ("sweeps_tc", ctypes.c_int),
-                ("batch_ticks", ctypes.c_longlong), ("batch_graph_launches", ctypes.c_int)]
+                ("batch_ticks", ctypes.c_longlong), ("batch_graph_launches", ctypes.c_int),
+                ("ms_v0", ctypes.c_double), ("pairs_delta", ctypes.c_longlong),
+                ("pairs_fp64", ctypes.c_longlong)]
 
 
 class GhsvdError(RuntimeError):
@@ -131,6 +133,11 @@ def load(path: str | None = None):
                                            ctypes.POINTER(vp), P64, vp]
     lib.ghsvd_align_phases.restype = c_int
     lib.ghsvd_align_phases.argtypes = [i64, vp, i64, vp, i64, vp]
+    lib.ghsvd_v0_targets.restype = c_int
+    lib.ghsvd_v0_targets.argtypes = [c_int, i64, vp, i64, ctypes.POINTER(vp), P64, vp,
+                                     ctypes.POINTER(ctypes.c_double), vp]
+    lib.ghsvd_v0_compose.restype = c_int
+    lib.ghsvd_v0_compose.argtypes = [c_int, i64, vp, ctypes.c_double, vp, i64, ctypes.POINTER(vp), P64, vp]
     lib.ghsvd_status_string.restype = ctypes.c_char_p
     lib.ghsvd_status_string.argtypes = [c_int]
     lib.ghsvd_urv.restype = c_int
@@ -492,6 +499,36 @@ def ghsvd_tc_block_ops(X, J, Z, stream=None):
     return gram
 
 
+def ghsvd_v0_targets(Vref, Vs, stream=None):
+    """Training targets (count x 2 n^2 FP32 CUDA tensor, normalized) and
+    their scale (the RMS) from aligned eigenvector sets Vs (include/ghsvd.h)."""
+    import torch
+    n = Vref.shape[0]
+    b = len(Vs)
+    T = torch.empty((b, 2 * n * n), dtype=torch.float32, device=Vref.device)
+    ptrs = (ctypes.c_void_p * b)(*[V.data_ptr() for V in Vs])
+    lds = (ctypes.c_int64 * b)(*[ld_of(V) for V in Vs])
+    rms = ctypes.c_double(0.0)
+    _check(load().ghsvd_v0_targets(b, n, Vref.data_ptr(), ld_of(Vref), ptrs, lds, T.data_ptr(),
+                                    ctypes.byref(rms), _stream_ptr(stream)))
+    return T, rms.value
+
+
+def ghsvd_v0_compose(Y, scale, Vref, stream=None):
+    """V0_i = Vref + scale * D_i from the MLP output rows Y (count x 2 n^2
+    FP32); returns the list of column-major complex128 CUDA tensors."""
+    import torch
+    n = Vref.shape[0]
+    b = Y.shape[0]
+    V0s = [torch.empty_strided((n, n), (1, n), dtype=torch.complex128, device=Vref.device)
+           for _ in range(b)]
+    ptrs = (ctypes.c_void_p * b)(*[V.data_ptr() for V in V0s])
+    lds = (ctypes.c_int64 * b)(*([n] * b))
+    _check(load().ghsvd_v0_compose(b, n, Y.contiguous().data_ptr(), float(scale), Vref.data_ptr(),
+                                    ld_of(Vref), ptrs, lds, _stream_ptr(stream)))
+    return V0s
+
+
 def ghsvd_align_phases(Vref, V, stream=None):
     """In place: align the phase of each column of V to the same column of Vref."""
     _check(load().ghsvd_align_phases(V.shape[1], Vref.data_ptr(), ld_of(Vref), V.data_ptr(),
@@ -522,7 +559,8 @@ def ghsvd_get_stats(h) -> dict:
                 ms_gram=st.ms_gram, ms_inner=st.ms_inner, ms_update=st.ms_update,
                 rounds_low=st.rounds_low, ms_phase2=st.ms_phase2, n2x2=st.n2x2,
                 sweeps_tc=st.sweeps_tc, batch_ticks=st.batch_ticks,
-                batch_graph_launches=st.batch_graph_launches)
+                batch_graph_launches=st.batch_graph_launches, ms_v0=st.ms_v0,
+                pairs_delta=st.pairs_delta, pairs_fp64=st.pairs_fp64)
 
 
 def ghsvd_urv(F, J, G, n_plus: int | None = None, stream=None):

@@ -39,13 +39,15 @@ class Family:
         return F, G
 
 
-def solve_many(solver, fam, ts, V0s=None, chunk=256):
+def solve_many(solver, fam, ts, V0s=None, chunk=256, times=None):
     """Batched solves of the family at the parameter vectors ts; returns
-    (lambdas, Vs, sweeps, statuses, seconds)."""
+    (lambdas, Vs, sweeps, statuses, seconds).  `times` (a dict) receives the
+    seconds spent applying the starting bases (ghsvd_stats.ms_v0)."""
     import time
 
     import torch
     lams, Vs, sweeps, statuses = [], [], [], []
+    v0_ms = 0.0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for a in range(0, len(ts), chunk):
@@ -53,38 +55,48 @@ def solve_many(solver, fam, ts, V0s=None, chunk=256):
         V0 = None if V0s is None else V0s[a:a + chunk]
         l, V, sw, st, _ = solver.solve_batched([F for F, _ in pairs], [G for _, G in pairs],
                                                [fam.J] * len(pairs), V0s=V0)
+        v0_ms += solver.stats()["ms_v0"] if V0 is not None else 0.0
         lams += l
         Vs += V
         sweeps += sw
         statuses += st
     torch.cuda.synchronize()
+    if times is not None:
+        times["v0_apply_s"] = times.get("v0_apply_s", 0.0) + v0_ms / 1e3
     return lams, Vs, sweeps, statuses, time.perf_counter() - t0
 
 
 def canonical_targets(Vs, Vref):
-    """Phase-align every V (sorted by eigenvalue) to Vref; return the real
-    training targets vec(V - Vref) as a (count x 2 n^2) float32 tensor."""
-    import torch
-    rows = []
+    """Phase-align every V (sorted by eigenvalue) to Vref; return the
+    normalized training targets vec(V - Vref) / scale (count x 2 n^2 FP32)
+    and the scale (ghsvd_align_phases, ghsvd_v0_targets)."""
     for V in Vs:
         ghsvd.ghsvd_align_phases(Vref, V)
-        D = (V - Vref).t().contiguous()                 # column-major order
-        rows.append(torch.view_as_real(D).reshape(-1).to(torch.float32))
-    return torch.stack(rows)
+    return ghsvd.ghsvd_v0_targets(Vref, Vs)
 
 
-def predict_v0(net, fam, Vref, ts, scale):
-    """V0(t) = Vref + scale * MLP(t), made S-orthonormal for G(t)."""
+def predict_v0(net, fam, Vref, ts, scale, times=None):
+    """V0(t) = Vref + scale * MLP(t) (ghsvd_mlp_forward, ghsvd_v0_compose),
+    made S-orthonormal for G(t) (ghsvd_s_orthonormalize).  `times` (a dict)
+    receives the seconds of the prediction and of the S-orthonormalization."""
+    import time
+
     import torch
-    n = fam.n
     X = torch.as_tensor(np.asarray(ts), dtype=torch.float32, device="cuda")
-    Y = net.forward(X) * scale
-    out, Gs = [], []
-    for i, t in enumerate(ts):
-        D = torch.view_as_complex(Y[i].to(torch.float64).reshape(n, n, 2)).t()
-        out.append(ghsvd.colmajor(Vref + D))
-        Gs.append(fam.at(t)[1])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Y = net.forward(X)
+    out = ghsvd.ghsvd_v0_compose(Y, scale, Vref)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    Gs = [fam.at(t)[1] for t in ts]                 # input synthesis of G(t)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
     ghsvd.ghsvd_s_orthonormalize(Gs, out)
+    torch.cuda.synchronize()
+    if times is not None:
+        times["predict_s"] = times.get("predict_s", 0.0) + (t1 - t0)
+        times["s_orthonormalize_s"] = times.get("s_orthonormalize_s", 0.0) + (time.perf_counter() - t2)
     return out
 
 

@@ -96,11 +96,10 @@ def test_learned_warm_start_end_to_end(gh):
     test_t = P.family_parameters(16, seed=12)
     _, Vs, _, st, _ = ws.solve_many(solver, fam, train_t, V0s=ws.reference_v0(fam, Vref, train_t))
     assert all(s == 0 for s in st)
-    T = ws.canonical_targets(Vs, Vref)
-    scale = float(T.std())
+    T, scale = ws.canonical_targets(Vs, Vref)         # normalized targets and their scale
     net = gh.Mlp(4, 64, T.shape[1], seed=3)
     X = torch.as_tensor(train_t, dtype=torch.float32, device="cuda")
-    loss = net.train(X, T / scale, epochs=400, batch=80, lr=2e-3)
+    loss = net.train(X, T, epochs=400, batch=80, lr=2e-3)
     assert loss < 0.2
     cold = ws.solve_many(solver, fam, test_t)
     learned = ws.solve_many(solver, fam, test_t, V0s=ws.predict_v0(net, fam, Vref, test_t, scale))
@@ -114,3 +113,23 @@ def test_learned_warm_start_end_to_end(gh):
         Fn, Gn = F.cpu().numpy(), G.cpu().numpy()
         tol = eig_tol_vec(Fn, Gn, J, lr_.cpu().numpy(), Fp.cpu().numpy())
         assert np.all(rel_err(lam.cpu().numpy(), lr_.cpu().numpy()) < tol)
+
+
+def test_v0_targets_and_compose_round_trip(gh):
+    # ghsvd_v0_targets then ghsvd_v0_compose with the targets themselves as
+    # the "prediction" gives the eigenvector sets back (FP32 differences)
+    rng = np.random.default_rng(5)
+    n = 48
+    def crand():
+        return torch.from_numpy(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).cuda()
+    Vref = gh.colmajor(crand())
+    Vs = [gh.colmajor(Vref + 0.01 * crand()) for _ in range(3)]
+    T, scale = gh.ghsvd_v0_targets(Vref, Vs)
+    assert T.shape == (3, 2 * n * n) and T.dtype == torch.float32
+    assert abs(float(torch.sqrt(torch.mean(T.double() ** 2))) - 1.0) < 1e-6
+    D = torch.stack([torch.view_as_real((V - Vref).t().contiguous()).reshape(-1) for V in Vs])
+    assert abs(scale - float(torch.sqrt(torch.mean(D ** 2)))) < 1e-9 * scale
+    V0s = gh.ghsvd_v0_compose(T, scale, Vref)
+    for V, V0 in zip(Vs, V0s):
+        assert V0.stride() == (1, n)
+        assert float((V0 - V).abs().max()) < 1e-7 * float((V - Vref).abs().max())
