@@ -78,7 +78,7 @@ __device__ __forceinline__ void c_left(T2 &x0, T2 &x1, const T *z)
 // complex64 preconditioning sweeps).  The 2x2 parameters (eq. 6.5-6.12) are
 // computed in FP64 from the pivot entries: correctly rounded step by step in
 // the FP64 sweeps (pivot2x2), with shared reciprocals in the complex64 sweeps
-// (pivot2x2_fast); with a.param32 the complex64 sweeps compute them in FP32
+// (pivot2x2_fast_x2, two lanes per pivot); with a.param32 the complex64 sweeps compute them in FP32
 // instead.  The complex64 sweeps count "big" by the FP64 test (sin(phi) or
 // sin(psi) >= 2^-27), which keeps the stagnation test of the mixed
 // schedule's refinement rounds as with exact FP64 parameters.
@@ -160,32 +160,39 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
         if (tid == 0) s_sweep = 0;
         __syncthreads();
         for (int r = 0; r < kk - 1; ++r) {
-            // pivots of the step, spread over four warps (one per SM sub-partition)
+            // pivots of the step, spread over four warps (one per SM sub-partition);
+            // the complex64 sweeps' FP64 parameters take two lanes per pivot
+            // (pivot2x2_fast_x2), the other routines one
             const int warp = tid >> 5, lane = tid & 31;
+            const bool paired = sizeof(TU) == sizeof(float) && !a.param32;
+            const int pk = paired ? (lane & 1) : 0;
+            const unsigned pmask = 3u << (lane & 30);
             if (warp < 4) {
                 int step_all = 0;
-                for (int l = lane * 4 + warp; l < np; l += 128) {
+                for (int l = (paired ? lane >> 1 : lane) * 4 + warp; l < np; l += paired ? 64 : 128) {
                     int pa, pb;
                     rr_pair(kk, r, l, &pa, &pb);
-                    pslot[2 * l] = pa;
-                    pslot[2 * l + 1] = pb;
+                    if (pk == 0) {
+                        pslot[2 * l] = pa;
+                        pslot[2 * l + 1] = pb;
+                    }
                     int rc = PIV_NONE, big = 0;
                     TU zl[8];
                     if (valid[pa] && valid[pb]) {
                         const U2 hab = H[pa + INNER_LD * pb], sab = S[pa + INNER_LD * pb];
-                        if (sizeof(TU) == sizeof(float) && a.param32) {
+                        if (paired) {
+                            double zd[8];
+                            rc = pivot2x2_fast_x2(pk, pmask, (double)H[pa + INNER_LD * pa].x,
+                                                  (double)H[pb + INNER_LD * pb].x, (double)hab.x,
+                                                  (double)hab.y, (double)S[pa + INNER_LD * pa].x,
+                                                  (double)S[pb + INNER_LD * pb].x, (double)sab.x,
+                                                  (double)sab.y, a.tol, a.crit_mode, zd, &big);
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) zl[q] = (TU)zd[q];
+                        } else if (sizeof(TU) == sizeof(float) && a.param32) {
                             rc = pivot2x2<TU>(H[pa + INNER_LD * pa].x, H[pb + INNER_LD * pb].x, hab.x,
                                               hab.y, S[pa + INNER_LD * pa].x, S[pb + INNER_LD * pb].x,
                                               sab.x, sab.y, (TU)a.tol, a.crit_mode, zl, &big);
-                        } else if (sizeof(TU) == sizeof(float)) {
-                            double zd[8];
-                            rc = pivot2x2_fast((double)H[pa + INNER_LD * pa].x,
-                                               (double)H[pb + INNER_LD * pb].x, (double)hab.x,
-                                               (double)hab.y, (double)S[pa + INNER_LD * pa].x,
-                                               (double)S[pb + INNER_LD * pb].x, (double)sab.x,
-                                               (double)sab.y, a.tol, a.crit_mode, zd, &big);
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) zl[q] = (TU)zd[q];
                         } else {
                             double zd[8];
                             rc = pivot2x2<double>((double)H[pa + INNER_LD * pa].x,
@@ -201,6 +208,7 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                     // dependent at their rounding level alone; the FP64 sweeps
                     // that follow decide about rank deficiency
                     if (rc == PIV_ERR_RANK && sizeof(TU) == sizeof(float)) rc = PIV_NONE;
+                    if (pk != 0) continue;                  // the pair's second lane
                     if (rc < 0) {
                         atomicOr(&s_err, rc == PIV_ERR_RANK ? DEVERR_RANK : DEVERR_NONFINITE);
                         rc = PIV_NONE;

@@ -160,24 +160,42 @@ __device__ __forceinline__ int pivot2x2(T hpp, T hqq, T hpq_re, T hpq_im, T spp,
 // ulps, far below the complex64 data the parameters are applied to), and
 // "big" decided by sin(phi), sin(psi) >= 2^-27, the FP64 test on a cosine
 // rounding to 1.
-__device__ __forceinline__ int pivot2x2_fast(double hpp, double hqq, double hpq_re, double hpq_im,
-                                             double spp, double sqq, double spq_re, double spq_im,
-                                             double tol, int crit_mode, double z[8], int *big)
+//
+// It runs on two lanes (k = 0, 1 of a lane pair; m = the pair's mask).  An
+// FP64 warp instruction occupies a sub-partition's FP64 pipe for the same
+// time whatever its active lanes, and nearly every quantity of eq. 6.5-6.11
+// comes in a pair (the p and q sides, real and imaginary parts, phi and psi):
+// lane 0 computes one member, lane 1 the other, and the two swap by a
+// shuffle (measured on the one-lane form of the same formulas: eight
+// reciprocal square roots and about twice the products on the critical
+// path).  Both lanes return the same code, *big and z[0..7].
+__device__ __forceinline__ double pswap(double v, unsigned m) { return __shfl_xor_sync(m, v, 1); }
+
+__device__ __forceinline__ int pivot2x2_fast_x2(int k, unsigned m, double hpp, double hqq, double hpq_re,
+                                                double hpq_im, double spp, double sqq, double spq_re,
+                                                double spq_im, double tol, int crit_mode, double z[8],
+                                                int *big)
 {
     *big = 0;
     if (!(spp > 0.0) || !(sqq > 0.0)) return PIV_ERR_RANK;
     if (!isfinite(hpp) || !isfinite(hqq) || !isfinite(hpq_re) || !isfinite(hpq_im) ||
         !isfinite(spp) || !isfinite(sqq) || !isfinite(spq_re) || !isfinite(spq_im))
         return PIV_ERR_NONFINITE;
-    const double dp = rsqrt(spp), dq = rsqrt(sqq);       // Section 6.1.1
+    // Section 6.1.1 (lane 0: p, lane 1: q)
+    const double d = rsqrt(k ? sqq : spp), d_o = pswap(d, m);
+    const double dp = k ? d_o : d, dq = k ? d : d_o;
     const double dpq = dp * dq;
-    const double h11 = hpp * dp * dp, h22 = hqq * dq * dq;
-    const double h12r = hpq_re * dpq, h12i = hpq_im * dpq;
-    const double s12r = spq_re * dpq, s12i = spq_im * dpq;
+    const double hh = (k ? hqq : hpp) * d * d, hh_o = pswap(hh, m);
+    const double h11 = k ? hh_o : hh, h22 = k ? hh : hh_o;
+    const double ho = (k ? hpq_im : hpq_re) * dpq, so = (k ? spq_im : spq_re) * dpq;
+    const double ho_o = pswap(ho, m), so_o = pswap(so, m);
+    const double h12r = k ? ho_o : ho, h12i = k ? ho : ho_o;
+    const double s12r = k ? so_o : so, s12i = k ? so : so_o;
     const double a1 = fabs(h11), a2 = fabs(h22);
     const double hmax = fmax(a1, a2), hmin = fmin(a1, a2);
-    const double ah2 = h12r * h12r + h12i * h12i;          // |h_pq|^2
-    const double x2 = s12r * s12r + s12i * s12i;           // x^2
+    // |h_pq|^2 (lane 0) and x^2 (lane 1)
+    const double sq = k ? s12r * s12r + s12i * s12i : h12r * h12r + h12i * h12i, sq_o = pswap(sq, m);
+    const double ah2 = k ? sq_o : sq, x2 = k ? sq : sq_o;
     const double ch = crit_mode == 0 ? (hmax * tol) * (hmin * tol) : (hmax * tol) * hmin;
     const bool crit_h = crit_mode == 0 ? ah2 >= ch : ah2 >= ch * ch;
     if (!crit_h && !(x2 >= tol * tol)) return PIV_NONE;    // eq. 6.12
@@ -187,49 +205,66 @@ __device__ __forceinline__ int pivot2x2_fast(double hpp, double hqq, double hpq_
     if (x2 != 0.0) {
         const double ix = rsqrt(x2);
         x = x2 * ix;
-        e1r = s12r * ix;
-        e1i = s12i * ix;
+        const double e = (k ? s12i : s12r) * ix, e_o = pswap(e, m);
+        e1r = k ? e_o : e;
+        e1i = k ? e : e_o;
     }
-    const double t2 = (1.0 - x) * (1.0 + x);
+    const double pmx = k ? 1.0 + x : 1.0 - x;
+    const double t2 = pmx * pswap(pmx, m);                 // (1 - x)(1 + x)
     const double it = rsqrt(t2), t = t2 * it;
-    const double u = e1r * h12r + e1i * h12i;              // eq. 6.5
-    const double v = e1r * h12i - e1i * h12r;
+    // eq. 6.5: u (lane 0), v (lane 1)
+    const double uv = k ? e1r * h12i - e1i * h12r : e1r * h12r + e1i * h12i, uv_o = pswap(uv, m);
+    const double u = k ? uv_o : uv, v = k ? uv : uv_o;
     const double h = h22 - h11;
-    double z11r, z11i, z12r, z12i, z21r, z21i, z22r, z22i;
+    double zr0, zi0, zr1, zi1;      // lane 0: z11, z12; lane 1: z21, z22
     if (h == 0.0 && v == 0.0) {                             // Section 6.1.6
         const double c = 0.70710678118654752440;
         const double d1 = rsqrt(1.0 + x), d2 = rsqrt(1.0 - x);
-        z11r = c * d1;        z11i = 0.0;
-        z12r = -e1r * c * d2; z12i = -e1i * c * d2;
-        z21r = e1r * c * d1;  z21i = -e1i * c * d1;
-        z22r = c * d2;        z22i = 0.0;
+        if (k == 0) { zr0 = c * d1; zi0 = 0.0; zr1 = -e1r * c * d2; zi1 = -e1i * c * d2; }
+        else { zr0 = e1r * c * d1; zi0 = -e1i * c * d1; zr1 = c * d2; zi1 = 0.0; }
         *big = 1;
     } else {
         const double sigma = h >= 0.0 ? 1.0 : -1.0;        // eq. 6.6
         const double hv2 = h * h + 4.0 * v * v;
         const double ihv = rsqrt(hv2), hv = hv2 * ihv;
-        const double num = sigma * (2.0 * u - (h11 + h22) * x);   // eq. 6.7
-        const double den = t * hv;
+        // eq. 6.7: num (lane 0), den (lane 1)
+        const double nd = k ? t * hv : sigma * (2.0 * u - (h11 + h22) * x), nd_o = pswap(nd, m);
+        const double num = k ? nd_o : nd, den = k ? nd : nd_o;
         const double ir = rsqrt(num * num + den * den);
-        const double s2t = num * ir, c2t = den * ir;
-        const double cg = fabs(h) * ihv, sg = sigma * 2.0 * v * ihv;   // eq. 6.11
-        const double xs = x * s2t, tcc = t * cg * c2t;     // eq. 6.10
-        const double qphi = (1.0 + xs + tcc) * 0.5, qpsi = (1.0 - xs + tcc) * 0.5;
-        const double rphi = rsqrt(qphi), rpsi = rsqrt(qpsi);
-        const double cphi = qphi * rphi, cpsi = qpsi * rpsi;
-        const double ip = 0.5 * rpsi, iq = 0.5 * rphi;     // 1/(2 cos psi), 1/(2 cos phi)
+        const double sc = nd * ir, sc_o = pswap(sc, m);    // sin 2theta | cos 2theta
+        const double s2t = k ? sc_o : sc, c2t = k ? sc : sc_o;
+        // eq. 6.11: cos gamma (lane 0), sin gamma (lane 1)
+        const double gg = k ? sigma * 2.0 * v * ihv : fabs(h) * ihv, gg_o = pswap(gg, m);
+        const double cg = k ? gg_o : gg, sg = k ? gg : gg_o;
+        // eq. 6.10: x sin 2theta (lane 0), t cos gamma cos 2theta (lane 1)
+        const double xt = k ? t * cg * c2t : x * s2t, xt_o = pswap(xt, m);
+        const double xs = k ? xt_o : xt, tcc = k ? xt : xt_o;
+        const double q = k ? (1.0 - xs + tcc) * 0.5 : (1.0 + xs + tcc) * 0.5;   // phi | psi
+        const double r = rsqrt(q), c = q * r;             // 1/cos, cos
+        const double r_o = pswap(r, m);
+        const double ipq = 0.5 * r_o;                       // 1/(2 cos psi) | 1/(2 cos phi)
         const double tsc = t * sg * c2t;
-        const double ar = (s2t - x) * ip, ai = tsc * ip;
-        const double br = (s2t + x) * iq, bi = -tsc * iq;
-        z11r = cphi * it;                     z11i = 0.0;
-        z12r = (e1r * ar - e1i * ai) * it;    z12i = (e1r * ai + e1i * ar) * it;
-        z21r = -(e1r * br + e1i * bi) * it;   z21i = -(e1r * bi - e1i * br) * it;
-        z22r = cpsi * it;                     z22i = 0.0;
+        const double abr = (k ? s2t + x : s2t - x) * ipq;  // ar | br
+        const double abi = (k ? -tsc : tsc) * ipq;         // ai | bi
+        const double abr_o = pswap(abr, m), abi_o = pswap(abi, m);
+        const double ar = k ? abr_o : abr, ai = k ? abi_o : abi;
+        const double br = k ? abr : abr_o, bi = k ? abi : abi_o;
+        if (k == 0) {
+            zr0 = c * it;                    zi0 = 0.0;
+            zr1 = (e1r * ar - e1i * ai) * it; zi1 = (e1r * ai + e1i * ar) * it;
+        } else {
+            zr0 = -(e1r * br + e1i * bi) * it; zi0 = -(e1r * bi - e1i * br) * it;
+            zr1 = c * it;                      zi1 = 0.0;
+        }
         const double thr2 = 5.551115123125783e-17;         // (2^-27)^2
-        *big = ar * ar + ai * ai >= thr2 || br * br + bi * bi >= thr2;
+        const int own = abr * abr + abi * abi >= thr2;
+        *big = own | __shfl_xor_sync(m, own, 1);
     }
-    z[0] = dp * z11r; z[1] = dp * z11i; z[2] = dp * z12r; z[3] = dp * z12i;   // Z' = D0^ Z^
-    z[4] = dq * z21r; z[5] = dq * z21i; z[6] = dq * z22r; z[7] = dq * z22i;
+    // Z' = D0^ Z^: lane 0 scales the first row by dp, lane 1 the second by dq
+    zr0 *= d; zi0 *= d; zr1 *= d; zi1 *= d;
+    const double o0 = pswap(zr0, m), o1 = pswap(zi0, m), o2 = pswap(zr1, m), o3 = pswap(zi1, m);
+    if (k == 0) { z[0] = zr0; z[1] = zi0; z[2] = zr1; z[3] = zi1; z[4] = o0; z[5] = o1; z[6] = o2; z[7] = o3; }
+    else { z[0] = o0; z[1] = o1; z[2] = o2; z[3] = o3; z[4] = zr0; z[5] = zi0; z[6] = zr1; z[7] = zi1; }
     return PIV_TRANSFORM;
 }
 
