@@ -161,10 +161,10 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
         __syncthreads();
         for (int r = 0; r < kk - 1; ++r) {
             // pivots of the step, spread over four warps (one per SM sub-partition);
-            // the complex64 sweeps' FP64 parameters take two lanes per pivot
-            // (pivot2x2_fast_x2), the other routines one
+            // FP64 parameters take two lanes per pivot (pivot2x2_x2 in the FP64
+            // sweeps, pivot2x2_fast_x2 in the complex64 ones), FP32 ones one
             const int warp = tid >> 5, lane = tid & 31;
-            const bool paired = sizeof(TU) == sizeof(float) && !a.param32;
+            const bool paired = !(sizeof(TU) == sizeof(float) && a.param32);
             const int pk = paired ? (lane & 1) : 0;
             const unsigned pmask = 3u << (lane & 30);
             if (warp < 4) {
@@ -182,26 +182,24 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                         const U2 hab = H[pa + INNER_LD * pb], sab = S[pa + INNER_LD * pb];
                         if (paired) {
                             double zd[8];
-                            rc = pivot2x2_fast_x2(pk, pmask, (double)H[pa + INNER_LD * pa].x,
-                                                  (double)H[pb + INNER_LD * pb].x, (double)hab.x,
-                                                  (double)hab.y, (double)S[pa + INNER_LD * pa].x,
-                                                  (double)S[pb + INNER_LD * pb].x, (double)sab.x,
-                                                  (double)sab.y, a.tol, a.crit_mode, zd, &big);
+                            if (sizeof(TU) == sizeof(double))
+                                rc = pivot2x2_x2(pk, pmask, (double)H[pa + INNER_LD * pa].x,
+                                                 (double)H[pb + INNER_LD * pb].x, (double)hab.x,
+                                                 (double)hab.y, (double)S[pa + INNER_LD * pa].x,
+                                                 (double)S[pb + INNER_LD * pb].x, (double)sab.x,
+                                                 (double)sab.y, a.tol, a.crit_mode, zd, &big);
+                            else
+                                rc = pivot2x2_fast_x2(pk, pmask, (double)H[pa + INNER_LD * pa].x,
+                                                      (double)H[pb + INNER_LD * pb].x, (double)hab.x,
+                                                      (double)hab.y, (double)S[pa + INNER_LD * pa].x,
+                                                      (double)S[pb + INNER_LD * pb].x, (double)sab.x,
+                                                      (double)sab.y, a.tol, a.crit_mode, zd, &big);
 #pragma unroll
                             for (int q = 0; q < 8; ++q) zl[q] = (TU)zd[q];
-                        } else if (sizeof(TU) == sizeof(float) && a.param32) {
+                        } else {                        // complex64 sweeps, FP32 parameters
                             rc = pivot2x2<TU>(H[pa + INNER_LD * pa].x, H[pb + INNER_LD * pb].x, hab.x,
                                               hab.y, S[pa + INNER_LD * pa].x, S[pb + INNER_LD * pb].x,
                                               sab.x, sab.y, (TU)a.tol, a.crit_mode, zl, &big);
-                        } else {
-                            double zd[8];
-                            rc = pivot2x2<double>((double)H[pa + INNER_LD * pa].x,
-                                                  (double)H[pb + INNER_LD * pb].x, (double)hab.x,
-                                                  (double)hab.y, (double)S[pa + INNER_LD * pa].x,
-                                                  (double)S[pb + INNER_LD * pb].x, (double)sab.x,
-                                                  (double)sab.y, a.tol, a.crit_mode, zd, &big);
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) zl[q] = (TU)zd[q];
                         }
                     }
                     // complex64 preconditioning sweeps leave a pivot that looks

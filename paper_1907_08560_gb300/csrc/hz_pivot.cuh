@@ -153,6 +153,117 @@ __device__ __forceinline__ int pivot2x2(T hpp, T hqq, T hpq_re, T hpq_im, T spp,
     return PIV_TRANSFORM;
 }
 
+// The partner lane's value (lanes 2i, 2i+1 of the mask m).
+__device__ __forceinline__ double pswap(double v, unsigned m) { return __shfl_xor_sync(m, v, 1); }
+
+// pivot2x2<double> on two lanes (k = 0, 1 of a lane pair; m = the pair's
+// mask), for the FP64 sweeps: every value is formed by the same operations
+// as in pivot2x2, in the lane that owns it (lane 0: the p side, real parts,
+// phi; lane 1: the q side, imaginary parts, psi), and the two lanes swap by
+// shuffles.  The chain holds 10 divisions and 7 square roots instead of 17
+// and 11 (an FP64 warp instruction occupies the FP64 pipe for the same time
+// whatever its active lanes).  Both lanes return the same code, *big, z.
+__device__ __forceinline__ int pivot2x2_x2(int k, unsigned m, double hpp, double hqq, double hpq_re,
+                                           double hpq_im, double spp, double sqq, double spq_re,
+                                           double spq_im, double tol, int crit_mode, double z[8], int *big)
+{
+    const double one = 1.0, zero = 0.0, half = 0.5;
+    *big = 0;
+    if (!(spp > zero) || !(sqq > zero)) return PIV_ERR_RANK;
+    if (!isfinite(hpp) || !isfinite(hqq) || !isfinite(hpq_re) || !isfinite(hpq_im) ||
+        !isfinite(spp) || !isfinite(sqq) || !isfinite(spq_re) || !isfinite(spq_im))
+        return PIV_ERR_NONFINITE;
+    // Section 6.1.1
+    const double d = one / sqrt(k ? sqq : spp), d_o = pswap(d, m);
+    const double dp = k ? d_o : d, dq = k ? d : d_o;
+    const double dpq = dp * dq;
+    const double hh = mul_rn(mul_rn(k ? hqq : hpp, d), d), hh_o = pswap(hh, m);
+    const double h11 = k ? hh_o : hh, h22 = k ? hh : hh_o;
+    const double ho = (k ? hpq_im : hpq_re) * dpq, so = (k ? spq_im : spq_re) * dpq;
+    const double ho_o = pswap(ho, m), so_o = pswap(so, m);
+    const double h12r = k ? ho_o : ho, h12i = k ? ho : ho_o;
+    const double s12r = k ? so_o : so, s12i = k ? so : so_o;
+    // eq. 6.12 (lane 0: |h_pq|, sqrt(hmax); lane 1: x, sqrt(hmin))
+    const double a1 = fabs(h11), a2 = fabs(h22);
+    const double hmax = fmax(a1, a2), hmin = fmin(a1, a2);
+    const double hx = k ? hyp(s12r, s12i) : hyp(h12r, h12i), hx_o = pswap(hx, m);
+    const double ah12 = k ? hx_o : hx, x = k ? hx : hx_o;
+    bool crit_h;
+    if (crit_mode == 0) {
+        const double sr = sqrt(k ? hmin : hmax), sr_o = pswap(sr, m);
+        crit_h = ah12 >= ((k ? sr_o : sr) * tol) * (k ? sr : sr_o);
+    } else {
+        crit_h = ah12 >= (hmax * tol) * hmin;
+    }
+    if (!crit_h && !(x >= tol)) return PIV_NONE;
+    if (h12r == zero && h12i == zero && s12r == zero && s12i == zero) return PIV_NONE;
+    if (!(x < one)) return PIV_ERR_RANK;
+    // Section 6.1.2
+    double e1r = one, e1i = zero;
+    if (x != zero) {
+        const double e = (k ? s12i : s12r) / x, e_o = pswap(e, m);
+        e1r = k ? e_o : e;
+        e1i = k ? e : e_o;
+    }
+    const double pmx = k ? one + x : one - x;
+    const double t = sqrt(k ? pswap(pmx, m) * pmx : pmx * pswap(pmx, m));   // (1 - x)(1 + x)
+    // eq. 6.5 (lane 0: u, lane 1: v)
+    const double uv = k ? e1r * h12i - e1i * h12r : e1r * h12r + e1i * h12i, uv_o = pswap(uv, m);
+    const double u = k ? uv_o : uv, v = k ? uv : uv_o;
+    const double h = h22 - h11;
+    double zr0, zi0, zr1, zi1;      // lane 0: z11, z12; lane 1: z21, z22
+    if (h == zero && v == zero) {                           // Section 6.1.6
+        const double c = 0.70710678118654752440;
+        const double dd = one / sqrt(k ? one - x : one + x), dd_o = pswap(dd, m);
+        const double d1 = k ? dd_o : dd, d2 = k ? dd : dd_o;
+        if (k == 0) { zr0 = c * d1; zi0 = zero; zr1 = -e1r * c * d2; zi1 = -e1i * c * d2; }
+        else { zr0 = e1r * c * d1; zi0 = -e1i * c * d1; zr1 = c * d2; zi1 = zero; }
+        *big = 1;
+    } else {
+        const double sigma = h >= zero ? one : -one;        // eq. 6.6
+        const double hv = hyp(h, 2.0 * v);
+        // eq. 6.7 (lane 0: num, lane 1: den)
+        const double nd = k ? mul_rn(t, hv) : sigma * (2.0 * u - (h11 + h22) * x), nd_o = pswap(nd, m);
+        const double num = k ? nd_o : nd, den = k ? nd : nd_o;
+        const double r = hyp(num, den);
+        const double sc = nd / r, sc_o = pswap(sc, m);      // sin 2theta | cos 2theta
+        const double s2t = k ? sc_o : sc, c2t = k ? sc : sc_o;
+        // eq. 6.11 (lane 0: cos gamma, lane 1: sin gamma)
+        const double gg = k ? sigma * 2.0 * v / hv : fabs(h) / hv, gg_o = pswap(gg, m);
+        const double cg = k ? gg_o : gg, sg = k ? gg : gg_o;
+        // eq. 6.10 in the order of pivot2x2, without contraction
+        const double xt = k ? mul_rn(mul_rn(t, cg), c2t) : mul_rn(x, s2t), xt_o = pswap(xt, m);
+        const double xs = k ? xt_o : xt, tcc = k ? xt : xt_o;
+        const double cc = k ? sqrt(mul_rn(add_rn(sub_rn(one, xs), tcc), half))
+                            : sqrt(mul_rn(add_rn(add_rn(one, xs), tcc), half));   // cos phi | cos psi
+        const double cc_o = pswap(cc, m);
+        const double cphi = k ? cc_o : cc, cpsi = k ? cc : cc_o;
+        const double tsc = t * sg * c2t;
+        // lane 0: e^{i alpha} sin(phi) = ((s2t - x) + i tsc) / (2 cos psi)
+        // lane 1: e^{-i beta} sin(psi) = ((s2t + x) - i tsc) / (2 cos phi)
+        const double den2 = 2.0 * (k ? cphi : cpsi);
+        const double abr = (k ? s2t + x : s2t - x) / den2, abi = (k ? -tsc : tsc) / den2;
+        const double abr_o = pswap(abr, m), abi_o = pswap(abi, m);
+        const double ar = k ? abr_o : abr, ai = k ? abi_o : abi;
+        const double br = k ? abr : abr_o, bi = k ? abi : abi_o;
+        const double it = one / t;
+        if (k == 0) {
+            zr0 = cphi * it;                  zi0 = zero;
+            zr1 = (e1r * ar - e1i * ai) * it; zi1 = (e1r * ai + e1i * ar) * it;
+        } else {
+            zr0 = -(e1r * br + e1i * bi) * it; zi0 = -(e1r * bi - e1i * br) * it;
+            zr1 = cpsi * it;                   zi1 = zero;
+        }
+        *big = !(cphi == one && cpsi == one);               // Section 6.1.7
+    }
+    // Z' = D0^ Z^: lane 0 scales the first row by dp, lane 1 the second by dq
+    zr0 = d * zr0; zi0 = d * zi0; zr1 = d * zr1; zi1 = d * zi1;
+    const double o0 = pswap(zr0, m), o1 = pswap(zi0, m), o2 = pswap(zr1, m), o3 = pswap(zi1, m);
+    if (k == 0) { z[0] = zr0; z[1] = zi0; z[2] = zr1; z[3] = zi1; z[4] = o0; z[5] = o1; z[6] = o2; z[7] = o3; }
+    else { z[0] = o0; z[1] = o1; z[2] = o2; z[3] = o3; z[4] = zr0; z[5] = zi0; z[6] = zr1; z[7] = zi1; }
+    return PIV_TRANSFORM;
+}
+
 // The same 2x2 transformation with FP64 parameters for the complex64 sweeps
 // of the mixed schedule: the formulas of pivot2x2 with every square root and
 // division taken from one reciprocal square root (sqrt(q) = q rsqrt(q),
@@ -169,8 +280,6 @@ __device__ __forceinline__ int pivot2x2(T hpp, T hqq, T hpq_re, T hpq_im, T spp,
 // shuffle (measured on the one-lane form of the same formulas: eight
 // reciprocal square roots and about twice the products on the critical
 // path).  Both lanes return the same code, *big and z[0..7].
-__device__ __forceinline__ double pswap(double v, unsigned m) { return __shfl_xor_sync(m, v, 1); }
-
 __device__ __forceinline__ int pivot2x2_fast_x2(int k, unsigned m, double hpp, double hqq, double hpq_re,
                                                 double hpq_im, double spp, double sqq, double spq_re,
                                                 double spq_im, double tol, int crit_mode, double z[8],
