@@ -171,7 +171,10 @@ def run_batched(args):
     Fs = [ghsvd.colmajor(torch.from_numpy(F)).cuda() for F, _, _ in batch]
     Gs = [ghsvd.colmajor(torch.from_numpy(G)).cuda() for _, _, G in batch]
     Js = [torch.from_numpy(J).cuda() for _, J, _ in batch]
-    solver = ghsvd.Solver(0, block_width=0, max_sweeps=args.max_sweeps)
+    prec = ghsvd.GHSVD_PRECISION_MIXED if args.precision == "mixed" else ghsvd.GHSVD_PRECISION_FP64
+    # the complex64 sweep budget of the single-pencil mixed legs
+    mkw = {"mixed_max_sweeps": 60} if args.precision == "mixed" else {}
+    solver = ghsvd.Solver(0, block_width=0, max_sweeps=args.max_sweeps, precision=prec, **mkw)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         solver.solve_batched(Fs, Gs, Js, stream=stream)
@@ -188,8 +191,8 @@ def run_batched(args):
     clk = clocks.stop()
     t_batch = e0.elapsed_time(e1) / 1e3 / args.steps
     w = solver.stats()["block_width"]
-    # the same pencils one by one through ghsvd_solve, same block width
-    one = ghsvd.Solver(0, block_width=w, max_sweeps=args.max_sweeps)
+    # the same pencils one by one through ghsvd_solve, same block width and schedule
+    one = ghsvd.Solver(0, block_width=w, max_sweeps=args.max_sweeps, precision=prec, **mkw)
     one.solve(Fs[0], Gs[0], Js[0], stream=stream)
     torch.cuda.synchronize()
     s0 = torch.cuda.Event(enable_timing=True)
@@ -234,10 +237,13 @@ def run_batched(args):
                       f"[{args.batch_lo},{args.batch_hi}])",
             "value": len(batch) / t_batch, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
             "config": {"workload": f"batch of {len(batch)} pencils F 1.5n x n (20% -1 signs), "
                                    f"G 2n x n, cond(S) log-uniform [1e4,1e10], n uniform "
                                    f"[{args.batch_lo},{args.batch_hi}] (min {min(ns)}, max {max(ns)})",
+                       "precision": args.precision,
+                       "sweeps_complex64_total": bst["sweeps_low"], "rounds_complex64_total": bst["rounds_low"],
                        "block_width_autotuned": w, "sweeps_min": min(sweeps), "sweeps_max": max(sweeps),
                        "statuses": sorted(set(statuses))},
             "sequential": {"value": len(batch) / t_seq, "unit": "solves/s", "seconds": t_seq},

@@ -270,7 +270,15 @@ void ghsvd_destroy(ghsvd_t h);
  *                 status of every pencil.
  * The handle's block_width is used for every pencil; block_width = 0 picks
  * it from {8, 16, 32} by timing a few ticks of each (the autotuner); the
- * choice is reported in ghsvd_stats.block_width.  FP64 schedule only.
+ * choice is reported in ghsvd_stats.block_width.
+ * Precision: opts.precision FP64 or MIXED (other values: GHSVD_ERR_INVALID_ARG).
+ * With MIXED every pencil without a starting basis runs the mixed schedule
+ * of ghsvd_solve on its own clock: complex64 rounds (mixed_max_sweeps,
+ * mixed_param32 apply; the complex64 Grams and updates run on the CUDA
+ * cores, mixed_tc is not used), each ended by the FP64 product W Z'_low in
+ * the next tick, then FP64 sweeps to the stopping rule; pencils given a V0
+ * run the FP64 schedule.  ghsvd_stats.sweeps_low and rounds_low are the sums
+ * over the pencils.  delta_update is not used by batched solves.
  * Returns GHSVD_OK when every pencil converged, otherwise the status of the
  * first pencil that failed (or GHSVD_ERR_NOT_CONVERGED).
  */

@@ -791,7 +791,8 @@ extern "C" ghsvd_status ghsvd_solve_batched(ghsvd_t h, int batch, const int64_t 
 {
     if (!h || batch < 1 || !m || !p || !n || !F || !ldf || !G || !ldg || !lambda)
         return GHSVD_ERR_INVALID_ARG;
-    if (h->opts.precision != GHSVD_PRECISION_FP64) return GHSVD_ERR_INVALID_ARG;
+    if (h->opts.precision != GHSVD_PRECISION_FP64 && h->opts.precision != GHSVD_PRECISION_MIXED)
+        return GHSVD_ERR_INVALID_ARG;
     for (int i = 0; i < batch; ++i) {
         const int8_t *Ji = J ? J[i] : nullptr;
         const int64_t np_ = n_plus ? n_plus[i] : m[i];
@@ -811,18 +812,16 @@ extern "C" ghsvd_status ghsvd_solve_batched(ghsvd_t h, int batch, const int64_t 
     if (!h->batch) h->batch = hz_batch_new();
     if (!h->batch) { cudaSetDevice(prev); return GHSVD_ERR_NOMEM; }
     memset(&h->stats, 0, sizeof(h->stats));
-    int w = 0;
-    double ms = 0;
-    long long ticks = 0;
-    double ms_v0 = 0.0;
+    HzBatchInfo info{};
     ghsvd_status s = hz_batch_solve(h->batch, h->device, &h->opts, batch, m, p, n, F, ldf, J, n_plus,
-                                    G, ldg, V0, ldv0, lambda, V, ldv, sweeps, status, &w, &ms, &ticks, &ms_v0,
-                                    stream);
-    h->stats.ms_v0 = ms_v0;
-    h->stats.block_width = w;
-    h->stats.ms_total = ms;
-    h->stats.batch_ticks = ticks;
-    h->stats.batch_graph_launches = ticks > 0 ? 1 : 0;
+                                    G, ldg, V0, ldv0, lambda, V, ldv, sweeps, status, &info, stream);
+    h->stats.ms_v0 = info.ms_v0;
+    h->stats.block_width = info.w_chosen;
+    h->stats.ms_total = info.ms_solve;
+    h->stats.batch_ticks = info.ticks;
+    h->stats.batch_graph_launches = info.ticks > 0 ? 1 : 0;
+    h->stats.sweeps_low = (int)info.sweeps_low;
+    h->stats.rounds_low = (int)info.rounds_low;
     h->solved = false;          // ghsvd_get_factors refers to single solves
     cudaSetDevice(prev);
     return s;

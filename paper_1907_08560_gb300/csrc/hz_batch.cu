@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "../../include/ghsvd.h"
+#include "hz_gemm.cuh"
 #include "hz_gram.cuh"
 #include "hz_inner.cuh"
 #include "hz_update.cuh"
@@ -33,6 +34,8 @@ namespace hz {
 // Per-pencil device descriptor.
 struct BPencil {
     double2 *W;                 // [ld x n] stacked F', G', Z'
+    float2 *W32;                // [ld x n] complex64 copy (mixed schedule), or null
+    double2 *Wtmp;              // [ld x n] product W Z'_low (mixed schedule), or null
     long long ld;               // Mt
     const int8_t *Jrow;         // [m_pad]
     const int *slot;            // [nsteps][npairs][kk]
@@ -43,42 +46,59 @@ struct BPencil {
     int *err;                   // [2]
     int m_pad, p_pad, n_pad, n;
     int kk, npairs, nsteps, kc, chunks_h, chunks_s;
-    double tol;
+    double tol;                 // eps sqrt(n) of eq. 6.12 (FP64 sweeps)
+    double tol32;               // the same with the complex64 unit roundoff
+    double pivots_per_sweep;    // 2x2 pivots of one sweep
 };
 
-// Per-pencil state, advanced by the control kernel.
+// Per-pencil state, advanced by the control kernel.  phase 1: complex64
+// rounds of the mixed schedule, phase 0: FP64 sweeps.  pending != 0: the
+// round just ended; the next tick applies Z'_low to the FP64 factors
+// (1: another complex64 round follows, 2: the FP64 sweeps) and the pencil's
+// step kernels skip that tick.
 struct BState {
     int step, sweep, active, status;
+    int phase, pending, rounds, round_sweeps, sweeps_low;
+    unsigned long long prev_big;
 };
+
+// Pencils whose round ended: ctl[2] of them, listed in pend[0..), with the
+// product's 64 x 64 tiles numbered from toff[j] (toff[ctl[2]] = ctl[3] tiles).
 
 // Status codes the control kernel writes (mirror ghsvd_status).
 constexpr int BST_RUNNING = -1;
 
-__global__ void __launch_bounds__(128, 3)
+template <typename T>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 128 : 160, 3)
 gram_batched(const BPencil *__restrict__ P, const BState *__restrict__ S, const int4 *__restrict__ work)
 {
     const int4 w = work[blockIdx.x];
-    if (!S[w.x].active) return;
+    const BState st = S[w.x];
+    if (!st.active || st.pending || st.phase != (sizeof(T) == 4)) return;
     const BPencil &p = P[w.x];
-    const int r = S[w.x].step;
+    const int r = st.step;
     const int c = w.z;
     const bool isH = c < p.chunks_h;
     const int r0 = isH ? c * p.kc : p.m_pad + (c - p.chunks_h) * p.kc;
     const int r1 = isH ? min(r0 + p.kc, p.m_pad) : min(r0 + p.kc, p.m_pad + p.p_pad);
     const int cpp = p.chunks_h + p.chunks_s;
-    gram_body<double>(p.W, p.ld, p.Jrow, p.slot + ((long long)r * p.npairs + w.y) * p.kk, p.kk, r0,
-                      r1, isH, p.partial + ((long long)w.y * cpp + c) * (KKMAX * KKMAX));
+    using T2 = typename cplx<T>::t;
+    const T2 *Wt = sizeof(T) == 8 ? (const T2 *)p.W : (const T2 *)p.W32;
+    gram_body<T>(Wt, p.ld, p.Jrow, p.slot + ((long long)r * p.npairs + w.y) * p.kk, p.kk, r0, r1, isH,
+                 (T2 *)p.partial + ((long long)w.y * cpp + c) * (KKMAX * KKMAX));
 }
 
+template <typename T>
 __global__ void __launch_bounds__(1024)
 inner_batched(const BPencil *__restrict__ P, const BState *__restrict__ S, const int4 *__restrict__ work,
-              int inner_sweeps, int crit_mode)
+              int inner_sweeps, int crit_mode, int param32)
 {
     extern __shared__ unsigned char smraw_inner[];
     const int4 w = work[blockIdx.x];
-    if (!S[w.x].active) return;
+    const BState st = S[w.x];
+    if (!st.active || st.pending || st.phase != (sizeof(T) == 4)) return;
     const BPencil &p = P[w.x];
-    const int r = S[w.x].step;
+    const int r = st.step;
     InnerArgs a{};
     a.npairs = p.npairs;
     a.kk = p.kk;
@@ -86,24 +106,76 @@ inner_batched(const BPencil *__restrict__ P, const BState *__restrict__ S, const
     a.chunks_h = p.chunks_h;
     a.inner_sweeps = inner_sweeps;
     a.crit_mode = crit_mode;
-    a.tol = p.tol;
-    inner_body<double, double>(p.partial + (long long)w.y * a.cpp * (KKMAX * KKMAX),
-                               p.slot + ((long long)r * p.npairs + w.y) * p.kk, a,
-                               p.zhat + (long long)w.y * KKMAX * KKMAX, p.flag + w.y, p.cnt, p.err,
-                               smraw_inner);
+    a.tol = sizeof(T) == 8 ? p.tol : p.tol32;
+    a.param32 = param32;
+    using T2 = typename cplx<T>::t;
+    inner_body<T, T>((const T2 *)p.partial + (long long)w.y * a.cpp * (KKMAX * KKMAX),
+                     p.slot + ((long long)r * p.npairs + w.y) * p.kk, a,
+                     (T2 *)p.zhat + (long long)w.y * KKMAX * KKMAX, p.flag + w.y, p.cnt, p.err, smraw_inner);
 }
 
+template <typename T>
 __global__ void __launch_bounds__(256)
 update_batched(const BPencil *__restrict__ P, const BState *__restrict__ S, const int4 *__restrict__ work)
 {
     extern __shared__ unsigned char smraw[];
     const int4 w = work[blockIdx.x];
-    if (!S[w.x].active) return;
+    const BState st = S[w.x];
+    if (!st.active || st.pending || st.phase != (sizeof(T) == 4)) return;
     const BPencil &p = P[w.x];
     if (!p.flag[w.y]) return;
-    const int r = S[w.x].step;
-    update_body<double, double>(p.W, p.ld, p.slot + ((long long)r * p.npairs + w.y) * p.kk, p.kk,
-                                (long long)w.z * UPD_R, p.zhat + (long long)w.y * KKMAX * KKMAX, smraw);
+    const int r = st.step;
+    using T2 = typename cplx<T>::t;
+    T2 *Wt = sizeof(T) == 8 ? (T2 *)p.W : (T2 *)p.W32;
+    update_body<T, T>(Wt, p.ld, p.slot + ((long long)r * p.npairs + w.y) * p.kk, p.kk, (long long)w.z * UPD_R,
+                      (const T2 *)p.zhat + (long long)w.y * KKMAX * KKMAX, smraw);
+}
+
+// The round products W_i Z'_low,i -> Wtmp_i of the pencils listed in pend
+// (Z'_low: the complex64 rows of Z' in W32), one 64 x 64 tile per CTA
+// iteration over all their tiles.
+__global__ void __launch_bounds__(256)
+round_product_batched(const BPencil *__restrict__ P, const int *__restrict__ ctl, const int *__restrict__ pend,
+                      const int *__restrict__ toff)
+{
+    const int np = ctl[2], total = ctl[3];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int j = 0;
+        while (j + 1 < np && toff[j + 1] <= t) ++j;
+        const BPencil &p = P[pend[j]];
+        const int local = t - toff[j];
+        const int rt = (int)(p.ld / 64);
+        const long long row0 = (long long)(local % rt) * 64;
+        const int col0 = (local / rt) * 64;
+        const float2 *zlow = p.W32 + (p.m_pad + p.p_pad);
+        gemm_tile_3m<float2>(p.W, p.ld, zlow, p.ld, p.Wtmp, p.ld, p.n, row0, col0);
+    }
+}
+
+// After the products: W_i <- Wtmp_i, and for a pencil that starts another
+// complex64 round W32_i <- fl32(W_i) with Z' reset to I (pending 1).
+__global__ void round_finish_batched(const BPencil *__restrict__ P, const BState *__restrict__ S,
+                                     const int *__restrict__ ctl, const int *__restrict__ pend)
+{
+    const int np = ctl[2];
+    for (int j = blockIdx.y; j < np; j += gridDim.y) {
+        const int i = pend[j];
+        const BPencil &p = P[i];
+        const bool again = S[i].pending == 1;
+        const long long total = p.ld * p.n;
+        const long long z0 = p.m_pad + p.p_pad;
+        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+             e += (long long)gridDim.x * blockDim.x) {
+            const double2 v = p.Wtmp[e];
+            p.W[e] = v;
+            if (again) {
+                const long long r = e % p.ld, c = e / p.ld;
+                float2 f = make_float2((float)v.x, (float)v.y);
+                if (r >= z0) f = make_float2((r - z0) == c ? 1.0f : 0.0f, 0.0f);
+                p.W32[e] = f;
+            }
+        }
+    }
 }
 
 // One thread per pencil: advance the step; at the end of a sweep apply the
@@ -112,11 +184,20 @@ update_batched(const BPencil *__restrict__ P, const BState *__restrict__ S, cons
 // ctl[1] = ticks run.  Inside the solve's graph (loop != 0) the kernel also
 // decides on the device whether the graph's while loop runs another tick:
 // while some pencil is active and fewer than max_ticks ticks have run.
+//
+// Mixed schedule (the rules of the single solve): a complex64 round ends when
+// its big count levels off (more than 0.8 of the previous sweep's and below
+// 1 % of the pivots), when no pivot rotated, or at the complex64 sweep
+// budget; the pencil then waits one tick for the product W Z'_low and either
+// starts another round (at most two) or continues with FP64 sweeps.  The
+// pencils waiting for a product are listed for the next tick.
 __global__ void control_batched(const BPencil *__restrict__ P, BState *__restrict__ S, int batch,
-                                int max_sweeps, long long *__restrict__ hist, int hist_len,
-                                int *__restrict__ ctl, cudaGraphConditionalHandle loop_handle, int loop,
+                                int max_sweeps, int mixed_max_sweeps, long long *__restrict__ hist,
+                                int hist_len, int *__restrict__ ctl, int *__restrict__ pend,
+                                int *__restrict__ toff, cudaGraphConditionalHandle loop_handle, int loop,
                                 long long max_ticks)
 {
+    constexpr int kMaxRounds = 2;
     __shared__ int count;
     if (threadIdx.x == 0) count = 0;
     __syncthreads();
@@ -124,7 +205,13 @@ __global__ void control_batched(const BPencil *__restrict__ P, BState *__restric
         BState st = S[i];
         if (st.active) {
             const BPencil &p = P[i];
-            if (p.err[0] & DEVERR_RANK) { st.active = 0; st.status = GHSVD_ERR_RANK_DEFICIENT; }
+            if (st.pending) {
+                // this tick applied the round's product: resume
+                if (st.pending == 2) st.phase = 0;
+                st.pending = 0;
+                st.round_sweeps = 0;
+                st.prev_big = ~0ULL;
+            } else if (p.err[0] & DEVERR_RANK) { st.active = 0; st.status = GHSVD_ERR_RANK_DEFICIENT; }
             else if (p.err[0] & DEVERR_NONFINITE) { st.active = 0; st.status = GHSVD_ERR_NONFINITE; }
             else if (st.step == p.nsteps - 1) {
                 const unsigned long long all = p.cnt[0], big = p.cnt[1];
@@ -136,7 +223,19 @@ __global__ void control_batched(const BPencil *__restrict__ P, BState *__restric
                 p.cnt[0] = 0;
                 p.cnt[1] = 0;
                 st.step = 0;
-                if (big == 0) { st.active = 0; st.status = GHSVD_OK; }
+                if (st.phase == 1) {
+                    st.sweeps_low += 1;
+                    st.round_sweeps += 1;
+                    const bool plateau = st.round_sweeps >= 2 && (double)big > 0.8 * (double)st.prev_big &&
+                                         (double)big < 0.01 * p.pivots_per_sweep;
+                    st.prev_big = big;
+                    const bool budget = st.sweeps_low >= mixed_max_sweeps;
+                    if (all == 0 || plateau || budget) {
+                        st.rounds += 1;
+                        st.pending = (budget || all == 0 || st.round_sweeps <= 3 || st.rounds >= kMaxRounds) ? 2 : 1;
+                    }
+                    if (st.sweep >= max_sweeps && !st.pending) { st.active = 0; st.status = GHSVD_ERR_NOT_CONVERGED; }
+                } else if (big == 0) { st.active = 0; st.status = GHSVD_OK; }
                 else if (st.sweep >= max_sweeps) { st.active = 0; st.status = GHSVD_ERR_NOT_CONVERGED; }
             } else {
                 st.step += 1;
@@ -147,6 +246,19 @@ __global__ void control_batched(const BPencil *__restrict__ P, BState *__restric
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        // the pencils whose round just ended, with the tile offsets of their products
+        int np = 0, tiles = 0;
+        for (int i = 0; i < batch; ++i) {
+            if (!S[i].active || !S[i].pending) continue;
+            const BPencil &p = P[i];
+            pend[np] = i;
+            toff[np] = tiles;
+            tiles += (int)(p.ld / 64) * ((p.n + 63) / 64);
+            ++np;
+        }
+        toff[np] = tiles;
+        ctl[2] = np;
+        ctl[3] = tiles;
         ctl[0] = count;
         const int ticks = ctl[1] + 1;
         ctl[1] = ticks;
@@ -154,10 +266,17 @@ __global__ void control_batched(const BPencil *__restrict__ P, BState *__restric
     }
 }
 
-__global__ void state_init(BState *S, int batch)
+__global__ void state_init(const BPencil *__restrict__ P, BState *S, int batch)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < batch) { S[i].step = 0; S[i].sweep = 0; S[i].active = 1; S[i].status = BST_RUNNING; }
+    if (i < batch) {
+        BState st{};
+        st.active = 1;
+        st.status = BST_RUNNING;
+        st.phase = P[i].W32 != nullptr;
+        st.prev_big = ~0ULL;
+        S[i] = st;
+    }
 }
 
 }  // namespace hz
@@ -175,7 +294,9 @@ struct PlanP {
     int m, p, n, m_pad, p_pad, n_pad, nb, wb, kk, npairs, nsteps, kc, chunks_h, chunks_s;
     long long Mt;
     long long oW, oPart, oZhat, oFlag, oSlot, oJrow, oCnt, oErr, oLam, oGsc, oVn, oGc, oKap, oRank;
-    long long oTmp;             // W V0 of this pencil (warm starts only), or -1
+    long long oTmp;             // W V0 (warm start) or W Z'_low (mixed schedule), or -1
+    long long oW32;             // complex64 copy of W (mixed schedule), or -1
+    int mixed;                  // this pencil runs the mixed schedule
 };
 
 struct Plan {
@@ -201,8 +322,9 @@ int partition(int n, int w, std::vector<int> &off)
 }
 
 Plan make_plan(int batch, const int64_t *m, const int64_t *p, const int64_t *n, int w, int sms,
-               bool with_v0)
+               const void *const *V0, bool mixed)
 {
+    const bool with_v0 = V0 != nullptr;
     Plan pl;
     pl.w = w;
     pl.bytes = 0;
@@ -242,7 +364,10 @@ Plan make_plan(int batch, const int64_t *m, const int64_t *p, const int64_t *n, 
         q.oErr = carve(8);
         q.oLam = carve(8LL * q.n); q.oGsc = carve(8LL * q.n); q.oVn = carve(8LL * q.n);
         q.oGc = carve(8LL * q.n); q.oKap = carve(8); q.oRank = carve(4LL * q.n);
-        q.oTmp = with_v0 ? carve(16LL * q.Mt * q.n) : -1;
+        // the mixed schedule for every pencil without a starting basis
+        q.mixed = mixed && !(with_v0 && V0[i]) && q.n >= 2;
+        q.oTmp = (with_v0 || q.mixed) ? carve(16LL * q.Mt * q.n) : -1;
+        q.oW32 = q.mixed ? carve(8LL * q.Mt * q.n) : -1;
         pl.gram_work += q.npairs * cpp;
         pl.inner_work += q.npairs;
         pl.update_work += q.npairs * (int)(q.Mt / hz::UPD_R);
@@ -265,7 +390,8 @@ struct BatchBuffers {
     BState *d_state = nullptr;
     int4 *d_work = nullptr;
     long long *d_hist = nullptr;
-    int *d_active = nullptr;
+    int *d_active = nullptr;            // ctl[4]: active pencils, ticks, pending pencils, their tiles
+    int *d_pend = nullptr;              // [batch] pending pencils, [batch + 1] their tile offsets
     int cap_batch = 0;
     long long cap_work = 0;
 };
@@ -273,7 +399,7 @@ struct BatchBuffers {
 static void free_batch(BatchBuffers &b)
 {
     cudaFree(b.arena); cudaFree(b.d_pen); cudaFree(b.d_state); cudaFree(b.d_work);
-    cudaFree(b.d_hist); cudaFree(b.d_active);
+    cudaFree(b.d_hist); cudaFree(b.d_active); cudaFree(b.d_pend);
     b = BatchBuffers();
 }
 
@@ -304,14 +430,16 @@ static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, con
         bb.arena_bytes = pl.bytes;
     }
     if (batch > bb.cap_batch) {
-        cudaFree(bb.d_pen); cudaFree(bb.d_state); cudaFree(bb.d_hist);
-        bb.d_pen = nullptr; bb.d_state = nullptr; bb.d_hist = nullptr;
+        cudaFree(bb.d_pen); cudaFree(bb.d_state); cudaFree(bb.d_hist); cudaFree(bb.d_pend);
+        bb.d_pen = nullptr; bb.d_state = nullptr; bb.d_hist = nullptr; bb.d_pend = nullptr;
         BT_TRY(cudaMalloc((void **)&bb.d_pen, sizeof(BPencil) * batch));
         BT_TRY(cudaMalloc((void **)&bb.d_state, sizeof(BState) * batch));
         BT_TRY(cudaMalloc((void **)&bb.d_hist, sizeof(long long) * 2 * kHistLen * batch));
+        BT_TRY(cudaMalloc((void **)&bb.d_pend, sizeof(int) * (2 * batch + 1)));
         bb.cap_batch = batch;
     }
-    if (!bb.d_active) BT_TRY(cudaMalloc((void **)&bb.d_active, 2 * sizeof(int)));
+    if (!bb.d_active) BT_TRY(cudaMalloc((void **)&bb.d_active, 4 * sizeof(int)));
+    BT_TRY(cudaMemsetAsync(bb.d_active, 0, 4 * sizeof(int), st));
     const long long nwork = (long long)pl.gram_work + pl.inner_work + pl.update_work;
     if (nwork > bb.cap_work) {
         cudaFree(bb.d_work);
@@ -339,6 +467,10 @@ static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, con
         d.kk = q.kk; d.npairs = q.npairs; d.nsteps = q.nsteps; d.kc = q.kc;
         d.chunks_h = q.chunks_h; d.chunks_s = q.chunks_s;
         d.tol = tol_scale * ldexp(1.0, -53) * sqrt((double)q.n);
+        d.tol32 = tol_scale * ldexp(1.0, -24) * sqrt((double)q.n);
+        d.pivots_per_sweep = (double)q.nsteps * q.npairs * (q.kk / 2) * (q.kk - 1);
+        d.W32 = q.mixed ? (float2 *)(base + q.oW32) : nullptr;
+        d.Wtmp = q.oTmp >= 0 ? (double2 *)(base + q.oTmp) : nullptr;
         hp[i] = d;
         // schedule tables (host-built, as for a single pencil)
         std::vector<int> off;
@@ -362,6 +494,10 @@ static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, con
         BT_TRY(hz::launch_copyin(d.W, false, q.Mt, q.m, q.p, q.n, q.m_pad, q.p_pad, q.n_pad, F[i],
                                  ldf[i], G[i], ldg[i], nullptr, 0, d.err, st));
         BT_TRY(hz::launch_gnorm(d.W, q.Mt, q.m_pad, q.p_pad, q.n, (double *)(base + q.oGc), st));
+        if (q.mixed) {      // the first complex64 round starts from fl32(W) and Z' = I
+            BT_TRY(hz::launch_convert(d.W32, true, d.W, q.Mt * q.n, st));
+            BT_TRY(hz::launch_eye32(d.W32, q.Mt, q.m_pad + q.p_pad, q.n, q.n_pad, st));
+        }
     }
     // warm starts: (F V0, G V0) with Z' = V0 for every pencil that has a V0,
     // as one batched FP64 product and one batched copy
@@ -431,38 +567,66 @@ static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, con
     BT_TRY(cudaMemcpyAsync(bb.d_work, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice,
                            st));
     BT_TRY(cudaMemsetAsync(bb.d_hist, 0, sizeof(long long) * 2 * kHistLen * batch, st));
-    hz::state_init<<<(batch + 127) / 128, 128, 0, st>>>(bb.d_state, batch);
+    hz::state_init<<<(batch + 127) / 128, 128, 0, st>>>(bb.d_pen, bb.d_state, batch);
     BT_TRY(cudaGetLastError());
     return GHSVD_OK;
 }
 
-static cudaError_t enqueue_tick(const BatchBuffers &bb, const Plan &pl, int batch, int inner_sweeps,
-                                int crit_mode, int max_sweeps, cudaStream_t st,
-                                cudaGraphConditionalHandle loop_handle = 0, int loop = 0, long long max_ticks = 0)
+static cudaError_t enqueue_tick(const BatchBuffers &bb, const Plan &pl, int batch, const ghsvd_opts &o,
+                                int max_sweeps, cudaStream_t st, cudaGraphConditionalHandle loop_handle = 0,
+                                int loop = 0, long long max_ticks = 0)
 {
     const int4 *wg = bb.d_work;
     const int4 *wi = wg + pl.gram_work;
     const int4 *wu = wi + pl.inner_work;
     int kkmax = 2;
-    for (const PlanP &q : pl.pp) kkmax = std::max(kkmax, q.kk);
-    const int gthreads = hz::gram_threads_c128(kkmax);
-    hz::gram_batched<<<pl.gram_work, gthreads, 0, st>>>(bb.d_pen, bb.d_state, wg);
-    hz::inner_batched<<<pl.inner_work, 1024, hz::inner_smem_bytes(sizeof(double2)), st>>>(
-        bb.d_pen, bb.d_state, wi, inner_sweeps, crit_mode);
-    hz::update_batched<<<pl.update_work, 256, hz::update_smem(sizeof(double2)), st>>>(
+    bool mixed = false;
+    for (const PlanP &q : pl.pp) {
+        kkmax = std::max(kkmax, q.kk);
+        mixed |= q.mixed != 0;
+    }
+    int *pend = bb.d_pend, *toff = bb.d_pend + batch;
+    if (mixed) {
+        // the products of the rounds that ended in the previous tick
+        int sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        hz::round_product_batched<<<2 * sms, 256, 0, st>>>(bb.d_pen, bb.d_active, pend, toff);
+        hz::round_finish_batched<<<dim3(64, std::min(batch, 64)), 256, 0, st>>>(bb.d_pen, bb.d_state, bb.d_active,
+                                                                               pend);
+    }
+    hz::gram_batched<double><<<pl.gram_work, hz::gram_threads_c128(kkmax), 0, st>>>(bb.d_pen, bb.d_state, wg);
+    if (mixed)
+        hz::gram_batched<float><<<pl.gram_work, hz::gram_threads(kkmax), 0, st>>>(bb.d_pen, bb.d_state, wg);
+    hz::inner_batched<double><<<pl.inner_work, 1024, hz::inner_smem_bytes(sizeof(double2)), st>>>(
+        bb.d_pen, bb.d_state, wi, o.inner_sweeps, o.crit_mode, 0);
+    if (mixed)
+        hz::inner_batched<float><<<pl.inner_work, 1024, hz::inner_smem_bytes(sizeof(float2)), st>>>(
+            bb.d_pen, bb.d_state, wi, o.inner_sweeps, o.crit_mode, o.mixed_param32);
+    hz::update_batched<double><<<pl.update_work, 256, hz::update_smem(sizeof(double2)), st>>>(
         bb.d_pen, bb.d_state, wu);
-    hz::control_batched<<<1, 128, 0, st>>>(bb.d_pen, bb.d_state, batch, max_sweeps, bb.d_hist,
-                                           kHistLen, bb.d_active, loop_handle, loop, max_ticks);
+    if (mixed)
+        hz::update_batched<float><<<pl.update_work, 256, hz::update_smem(sizeof(float2)), st>>>(
+            bb.d_pen, bb.d_state, wu);
+    hz::control_batched<<<1, 128, 0, st>>>(bb.d_pen, bb.d_state, batch, max_sweeps, o.mixed_max_sweeps, bb.d_hist, kHistLen,
+                                           bb.d_active, pend, toff, loop_handle, loop, max_ticks);
     return cudaGetLastError();
 }
 
 static cudaError_t batch_attributes()
 {
-    cudaError_t e = cudaFuncSetAttribute(hz::inner_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(hz::inner_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)hz::inner_smem_bytes(sizeof(double2)));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(hz::update_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)hz::update_smem(sizeof(double2)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(hz::inner_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)hz::inner_smem_bytes(sizeof(float2)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(hz::update_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)hz::update_smem(sizeof(double2)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(hz::update_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)hz::update_smem(sizeof(float2)));
+    return e;
 }
 
 // Run ticks until no pencil is active, as one graph launch: the graph is a
@@ -490,8 +654,7 @@ static ghsvd_status run_ticks(BatchBuffers &bb, const Plan &pl, int batch, const
         cudaGraph_t body = np.conditional.phGraph_out[0];
         e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t ec = enqueue_tick(bb, pl, batch, o.inner_sweeps, o.crit_mode, o.max_sweeps, cs, handle, 1,
-                                          max_ticks);
+            cudaError_t ec = enqueue_tick(bb, pl, batch, o, o.max_sweeps, cs, handle, 1, max_ticks);
             cudaGraph_t captured = nullptr;
             e = cudaStreamEndCapture(cs, &captured);
             if (e == cudaSuccess) e = ec;
@@ -521,19 +684,19 @@ void hz_batch_free(void *p)
     delete b;
 }
 
-ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, int batch,
-                                                 const int64_t *m, const int64_t *p, const int64_t *n,
-                                                 const void *const *F, const int64_t *ldf,
-                                                 const int8_t *const *J, const int64_t *n_plus,
-                                                 const void *const *G, const int64_t *ldg,
-                                                 const void *const *V0, const int64_t *ldv0,
-                                                 double *const *lambda, void *const *V,
-                                                 const int64_t *ldv, int *sweeps, int *status,
-                                                 int *w_chosen, double *ms_solve, long long *ticks_out,
-                                                 double *ms_v0, void *stream)
+ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, int batch, const int64_t *m,
+                            const int64_t *p, const int64_t *n, const void *const *F, const int64_t *ldf,
+                            const int8_t *const *J, const int64_t *n_plus, const void *const *G,
+                            const int64_t *ldg, const void *const *V0, const int64_t *ldv0,
+                            double *const *lambda, void *const *V, const int64_t *ldv, int *sweeps, int *status,
+                            HzBatchInfo *info, void *stream)
 {
     BatchBuffers &bb = *(BatchBuffers *)buffers;
     const ghsvd_opts &o = *opts;
+    const bool mixed = o.precision == GHSVD_PRECISION_MIXED;
+    HzBatchInfo dummy{};
+    if (!info) info = &dummy;
+    *info = HzBatchInfo{};
     cudaStream_t st = (cudaStream_t)stream;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
@@ -547,7 +710,7 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
         double best = 1e300;
         w = 32;
         for (int c : cands) {
-            Plan pl = make_plan(batch, m, p, n, c, sms, V0 != nullptr);
+            Plan pl = make_plan(batch, m, p, n, c, sms, V0, mixed);
             ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, V0, ldv0, st, opts->tol_scale);
             if (s != GHSVD_OK) return s;
             cudaEvent_t e0, e1;
@@ -555,9 +718,9 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
             cudaEventCreate(&e1);
             const int probe = 4;
             // warm-up tick, then time `probe` ticks
-            enqueue_tick(bb, pl, batch, o.inner_sweeps, o.crit_mode, 1 << 30, st);
+            enqueue_tick(bb, pl, batch, o, 1 << 30, st);
             cudaEventRecord(e0, st);
-            for (int t = 0; t < probe; ++t) enqueue_tick(bb, pl, batch, o.inner_sweeps, o.crit_mode, 1 << 30, st);
+            for (int t = 0; t < probe; ++t) enqueue_tick(bb, pl, batch, o, 1 << 30, st);
             cudaEventRecord(e1, st);
             cudaError_t e = cudaEventSynchronize(e1);
             float ms = 0;
@@ -572,10 +735,11 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
             if (sweep_ms < best) { best = sweep_ms; w = c; }
         }
     }
-    if (w_chosen) *w_chosen = w;
-    Plan pl = make_plan(batch, m, p, n, w, sms, V0 != nullptr);
+    info->w_chosen = w;
+    Plan pl = make_plan(batch, m, p, n, w, sms, V0, mixed);
     auto t0 = std::chrono::steady_clock::now();
-    ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, V0, ldv0, st, opts->tol_scale, ms_v0);
+    ghsvd_status s = setup_batch(bb, pl, batch, F, ldf, J, n_plus, G, ldg, V0, ldv0, st, opts->tol_scale,
+                                 &info->ms_v0);
     if (s != GHSVD_OK) return s;
     // bad J entries or non-finite inputs
     std::vector<int> herr(2 * batch, 0);
@@ -590,9 +754,10 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
     long long max_ticks = 0;
     for (const PlanP &q : pl.pp) max_ticks = std::max<long long>(max_ticks, (long long)q.nsteps * o.max_sweeps);
     long long ticks = 0;
+    // + one tick per round product of the mixed schedule
     s = run_ticks(bb, pl, batch, o, st, max_ticks + 16, &ticks);
     if (s != GHSVD_OK) return s;
-    if (ticks_out) *ticks_out = ticks;
+    info->ticks = ticks;
     std::vector<BState> hs(batch);
     if (cudaMemcpyAsync(hs.data(), bb.d_state, sizeof(BState) * batch, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return GHSVD_ERR_CUDA;
@@ -611,8 +776,7 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
         if (cudaMemcpyAsync(&herr[2 * i], bb.arena + pl.pp[i].oErr, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
             return GHSVD_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return GHSVD_ERR_CUDA;
-    if (ms_solve)
-        *ms_solve = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    info->ms_solve = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     ghsvd_status worst = GHSVD_OK;
     for (int i = 0; i < batch; ++i) {
         int stt = hs[i].status;
@@ -621,6 +785,8 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
         if (herr[2 * i] & hz::DEVERR_NONFINITE) stt = GHSVD_ERR_NONFINITE;
         if (status) status[i] = stt;
         if (sweeps) sweeps[i] = hs[i].sweep;
+        info->sweeps_low += hs[i].sweeps_low;
+        info->rounds_low += hs[i].rounds;
         if (stt != GHSVD_OK && (worst == GHSVD_OK || worst == GHSVD_ERR_NOT_CONVERGED))
             worst = (ghsvd_status)stt;
     }

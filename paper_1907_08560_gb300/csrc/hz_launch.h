@@ -193,6 +193,15 @@ cudaError_t launch_permute_rows(const double2 *src, long long lds, int n, const 
 
 // Batched solves (hz_batch.cu).
 #include "../../include/ghsvd.h"
+// What a batched solve reports beside the per-pencil results.
+struct HzBatchInfo {
+    int w_chosen;               // block width used
+    double ms_solve;            // wall time from set-up to the outputs
+    long long ticks;            // ticks run on the device
+    double ms_v0;               // applying the starting bases
+    long long sweeps_low;       // complex64 sweeps over all pencils (mixed schedule)
+    long long rounds_low;       // complex64 rounds over all pencils
+};
 void *hz_batch_new();
 void hz_batch_free(void *buffers);
 ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, int batch,
@@ -200,5 +209,4 @@ ghsvd_status hz_batch_solve(void *buffers, int device, const ghsvd_opts *opts, i
                             const void *const *F, const int64_t *ldf, const int8_t *const *J,
                             const int64_t *n_plus, const void *const *G, const int64_t *ldg,
                             const void *const *V0, const int64_t *ldv0, double *const *lambda, void *const *V, const int64_t *ldv, int *sweeps,
-                            int *status, int *w_chosen, double *ms_solve, long long *ticks, double *ms_v0,
-                            void *stream);
+                            int *status, HzBatchInfo *info, void *stream);

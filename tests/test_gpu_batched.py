@@ -142,3 +142,73 @@ def test_batched_kpoint_pencils_match_oracle_golden(gh):
     assert st == gh.GHSVD_OK and all(x == 0 for x in statuses)
     for g, lam in zip(goldens, lams):
         assert golden_ratio(lam.cpu().numpy(), g) < 1.0, g["name"]
+
+
+@pytest.mark.parametrize("w,param32", [(8, 0), (16, 0), (16, 1)])
+def test_batched_mixed_schedule_matches_oracle_per_pencil(gh, w, param32):
+    # every pencil runs its own complex64 rounds (Z'_low accumulated in
+    # complex64, applied to the FP64 factors by one FP64 product per round)
+    # and then FP64 sweeps to the stopping rule of Section 6.1.7
+    batch = small_batch()
+    s = gh.Solver(0, block_width=w, precision=gh.GHSVD_PRECISION_MIXED, mixed_param32=param32,
+                  max_sweeps=80)
+    lams, Vs, sweeps, statuses, st = s.solve_batched(
+        [dev(gh, F) for F, _, _ in batch], [dev(gh, G) for _, _, G in batch],
+        [torch.from_numpy(J).cuda() for _, J, _ in batch])
+    assert st == gh.GHSVD_OK and all(x == 0 for x in statuses)
+    stt = s.stats()
+    assert stt["rounds_low"] >= len(batch)          # at least one round per pencil
+    assert stt["sweeps_low"] >= len(batch)
+    assert stt["batch_graph_launches"] == 1
+    for (F, J, G), lam, V in zip(batch, lams, Vs):
+        ref = oracle.solve(F, G, J, method="blocked", w=w)
+        assert ref["status"] == 0
+        tol = eig_tol_vec(F, G, J, ref["lam"], ref["F"])
+        assert np.all(rel_err(lam.cpu().numpy(), ref["lam"]) < tol)
+        GV = G @ V.cpu().numpy()
+        assert np.max(np.abs(GV.conj().T @ GV - np.eye(F.shape[1]))) < 1e-8
+
+
+def test_batched_mixed_with_starting_basis_keeps_fp64_for_that_pencil(gh):
+    # a pencil given a starting Z' runs the FP64 schedule; the others the mixed one
+    batch = small_batch()[:3]
+    n0 = batch[0][0].shape[1]
+    V0 = gh.colmajor(torch.eye(n0, dtype=torch.complex128)).cuda()
+    s = gh.Solver(0, block_width=8, precision=gh.GHSVD_PRECISION_MIXED)
+    lams, _, sweeps, statuses, st = s.solve_batched(
+        [dev(gh, F) for F, _, _ in batch], [dev(gh, G) for _, _, G in batch],
+        [torch.from_numpy(J).cuda() for _, J, _ in batch], want_vectors=False,
+        V0s=[V0, None, None])
+    assert st == gh.GHSVD_OK
+    for (F, J, G), lam in zip(batch, lams):
+        ref = oracle.solve(F, G, J, method="blocked", w=8)
+        tol = eig_tol_vec(F, G, J, ref["lam"], ref["F"])
+        assert np.all(rel_err(lam.cpu().numpy(), ref["lam"]) < tol)
+    # the pencil with the starting basis runs exactly as in an FP64 batched
+    # solve of the same pencils (same plan, same arithmetic): bitwise equal
+    one = gh.Solver(0, block_width=8)
+    l1, _, sw1, _, _ = one.solve_batched(
+        [dev(gh, F) for F, _, _ in batch], [dev(gh, G) for _, _, G in batch],
+        [torch.from_numpy(J).cuda() for _, J, _ in batch], want_vectors=False,
+        V0s=[V0, None, None])
+    assert sweeps[0] == sw1[0]
+    assert torch.equal(lams[0], l1[0])
+    assert s.stats()["rounds_low"] >= 2 and one.stats()["rounds_low"] == 0
+
+
+def test_batched_mixed_kpoint_pencils_match_oracle_golden(gh):
+    # the three k-point pencils of the golden test, mixed schedule
+    from conftest import fullsize_golden, golden_ratio
+    names = ("kpt56", "kpt11", "kpt23")
+    goldens = [fullsize_golden(nm) for nm in names]
+    pens = [P.batch_pencil(g["n"], g["cond_s"], g["seed"]) for g in goldens]
+    s = gh.Solver(0, block_width=32, max_sweeps=80, precision=gh.GHSVD_PRECISION_MIXED)
+    lams, _, sweeps, statuses, st = s.solve_batched(
+        [dev(gh, F) for F, _, _ in pens], [dev(gh, G) for _, _, G in pens],
+        [torch.from_numpy(J).cuda() for _, J, _ in pens], want_vectors=False)
+    stt = s.stats()
+    s.close()
+    assert st == gh.GHSVD_OK and all(x == 0 for x in statuses)
+    assert stt["sweeps_low"] >= 3
+    for g, lam in zip(goldens, lams):
+        assert golden_ratio(lam.cpu().numpy(), g) < 1.0, g["name"]
