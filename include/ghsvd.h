@@ -133,8 +133,9 @@ typedef struct {
     int delta_update;    /* FP64 sweeps: 1 (default) updates every pair whose
                             Z^ - I has all entries <= 2^-29 in the delta form
                             X + X (Z^ - I), the product from FP32 roundings by
-                            FP32 FMAs, the sum in FP64 (as accurate as the FP64
-                            product: its error stays below 2^-53 |X|); the
+                            FP32 FMAs, the sum in FP64 (error bound about
+                            2^-47 sum_l |x_il| per entry, the size of the FP64
+                            product's bound for rows of comparable entries); the
                             other pairs, and every pair with 0, by the FP64
                             product                                           */
 } ghsvd_opts;

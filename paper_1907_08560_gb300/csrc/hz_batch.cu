@@ -336,7 +336,11 @@ Plan make_plan(int batch, const int64_t *m, const int64_t *p, const int64_t *n, 
         const int nbi = partition((int)n[i], std::min<int>(w, (int)n[i]), off);
         pair_rows += (long long)(nbi / 2) * (rup(m[i], hz::ROWPAD) + rup(p[i], hz::ROWPAD));
     }
-    const int kc_all = (int)std::min<long long>(4096, std::max<long long>(256, rup(pair_rows / (4LL * sms), 64)));
+    // (the complex64 sweeps of the mixed schedule sum their Gram partials in
+    // FP32: chunks of at most 512 rows keep that rounding noise near the
+    // single-pencil solve's, so that their rounds level off as there)
+    const long long kc_cap = mixed ? 512 : 4096;
+    const int kc_all = (int)std::min<long long>(kc_cap, std::max<long long>(256, rup(pair_rows / (4LL * sms), 64)));
     for (int i = 0; i < batch; ++i) {
         PlanP q{};
         q.m = (int)m[i]; q.p = (int)p[i]; q.n = (int)n[i];

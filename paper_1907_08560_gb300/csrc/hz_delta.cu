@@ -4,12 +4,15 @@
 // with the product X E formed from FP32 roundings of X and E by FP32 FMAs and
 // the sum taken in FP64.
 //
-// Accuracy: the FP32 product carries an error of a few units of 2^-24
-// relative to |X||E| (rounding of X and E, FP32 accumulation); with every
-// entry of E at most DELTA_E = 2^-29 in real and imaginary part, that is below
-// 2^-53 |X| per entry, the rounding of the FP64 sum itself -- the update is as
-// accurate as the FP64 product of update_kernel<double>, and the sum is exact
-// for an untouched column (E's column zero).  Late in an iteration most pairs
+// Accuracy: the FP32 product's error per entry is at most about
+// (kk + 2) 2^-24 sum_l |x_il||e_lj| (rounding of X and E, FP32 accumulation of
+// kk terms); with every entry of E at most DELTA_E = 2^-29 in real and
+// imaginary part that is about 2^-47 sum_l |x_il| at kk = 64.  The FP64
+// product's own bound, gamma_kk sum_l |x_il||z_lj|, is about 2^-47 |x_ij|:
+// the two have the same size for the rows of comparable entries the stacked
+// factors hold, and the typical (random-walk) error of the FP32 product is
+// far below its bound.  The sum is exact for an untouched column (E's column
+// zero).  Late in an iteration most pairs
 // rotate by far less than that (the big/small test of Section 6.1.7 already
 // calls every rotation with sin < 2^-27 small), and the FP32 pipe of this GPU
 // is 64 times faster than its FP64 pipe, so the update of those pairs becomes

@@ -114,7 +114,10 @@ __device__ __forceinline__ void update_body_3m(double2 *__restrict__ W, long lon
 }
 
 // The complex64 body (four real FMA chains per output; the FP32 pipe does
-// not bound it).
+// not bound it), in the delta form X + X (Z^ - I): the rounding error of the
+// product is then relative to |X||Z^ - I| instead of |X||Z^|, so that the
+// small rotations of a converging sweep add little rounding noise, and a
+// column whose Z^ column is e_j stays exactly as it was.
 template <typename T, typename TZ>
 __device__ __forceinline__ void update_body_4m(typename cplx<T>::t *__restrict__ W, long long ld,
                                                const int *__restrict__ slot, int kk, long long row0,
@@ -150,6 +153,8 @@ __device__ __forceinline__ void update_body_4m(typename cplx<T>::t *__restrict__
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
+    if (tid < kk) zs[tid * UPD_LD + tid].x -= (T)1;   // E = Z^ - I (exact near 1)
+    __syncthreads();
     T accr[4][4], acci[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -176,10 +181,11 @@ __device__ __forceinline__ void update_body_4m(typename cplx<T>::t *__restrict__
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
+            T2 &o = xs[(ty + 16 * i) * UPD_LD + tx + 16 * j];   // read, then written, by this thread only
             T2 v;
-            v.x = accr[i][j];
-            v.y = acci[i][j];
-            xs[(ty + 16 * i) * UPD_LD + tx + 16 * j] = v;
+            v.x = o.x + accr[i][j];
+            v.y = o.y + acci[i][j];
+            o = v;
         }
     __syncthreads();
     for (int idx = tid; idx < UPD_R * KKMAX; idx += 256) {

@@ -79,13 +79,14 @@ def test_fullsize_fp64_matches_oracle(fp64):
     assert golden_ratio(fp64["lam"].cpu().numpy(), g) < 1.0
 
 
-@pytest.mark.parametrize("kind", ["mixed", "mixed_param32", "shortened"])
+@pytest.mark.parametrize("kind", ["mixed", "mixed_param32", "mixed_cuda_cores", "shortened"])
 def test_fullsize_variants_match_oracle_and_fp64(fp64, kind):
     gh = fp64["gh"]
     opts = dict(block_width=32, max_sweeps=80)
     if kind.startswith("mixed"):
         opts.update(precision=gh.GHSVD_PRECISION_MIXED, mixed_max_sweeps=60,
-                    mixed_param32=int(kind == "mixed_param32"))
+                    mixed_param32=int(kind == "mixed_param32"),
+                    mixed_tc=int(kind != "mixed_cuda_cores"))
     else:
         opts.update(shorten=1)
     s = gh.Solver(0, **opts)
