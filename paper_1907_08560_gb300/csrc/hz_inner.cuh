@@ -42,25 +42,29 @@ __device__ __forceinline__ T2 c_make(T x, T y)
 }
 
 // [x0 x1] <- [x0 x1] Z, Z = {z11, z12; z21, z22} given as z[0..7] (re, im).
+// z11 and z22 are real (z[1] = z[7] = 0): eq. 6.9 with the phases moved off
+// the diagonal (Section 6.1.5), scaled by the real D0 of Section 6.1.1; the
+// terms with z[1] and z[7] are left out (12 real products instead of 16).
 template <typename T2, typename T>
 __device__ __forceinline__ void c_right(T2 &x0, T2 &x1, const T *z)
 {
     const T2 a = x0, b = x1;
-    x0.x = a.x * z[0] - a.y * z[1] + b.x * z[4] - b.y * z[5];
-    x0.y = a.x * z[1] + a.y * z[0] + b.x * z[5] + b.y * z[4];
-    x1.x = a.x * z[2] - a.y * z[3] + b.x * z[6] - b.y * z[7];
-    x1.y = a.x * z[3] + a.y * z[2] + b.x * z[7] + b.y * z[6];
+    x0.x = a.x * z[0] + b.x * z[4] - b.y * z[5];
+    x0.y = a.y * z[0] + b.x * z[5] + b.y * z[4];
+    x1.x = a.x * z[2] - a.y * z[3] + b.x * z[6];
+    x1.y = a.x * z[3] + a.y * z[2] + b.y * z[6];
 }
 
-// [x0; x1] <- Z^* [x0; x1] (Z^* = {conj z11, conj z21; conj z12, conj z22}).
+// [x0; x1] <- Z^* [x0; x1] (Z^* = {conj z11, conj z21; conj z12, conj z22}),
+// z11 and z22 real as above.
 template <typename T2, typename T>
 __device__ __forceinline__ void c_left(T2 &x0, T2 &x1, const T *z)
 {
     const T2 a = x0, b = x1;
-    x0.x = z[0] * a.x + z[1] * a.y + z[4] * b.x + z[5] * b.y;
-    x0.y = z[0] * a.y - z[1] * a.x + z[4] * b.y - z[5] * b.x;
-    x1.x = z[2] * a.x + z[3] * a.y + z[6] * b.x + z[7] * b.y;
-    x1.y = z[2] * a.y - z[3] * a.x + z[6] * b.y - z[7] * b.x;
+    x0.x = z[0] * a.x + z[4] * b.x + z[5] * b.y;
+    x0.y = z[0] * a.y + z[4] * b.y - z[5] * b.x;
+    x1.x = z[2] * a.x + z[3] * a.y + z[6] * b.x;
+    x1.y = z[2] * a.y - z[3] * a.x + z[6] * b.y;
 }
 
 // ---------------------------------------------------------------------------
@@ -178,24 +182,20 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                     }
                     int rc = PIV_NONE, big = 0;
                     TU zl[8];
+                    double zrow[4];                     // paired: this lane's row of Z'
                     if (valid[pa] && valid[pb]) {
                         const U2 hab = H[pa + INNER_LD * pb], sab = S[pa + INNER_LD * pb];
                         if (paired) {
-                            double zd[8];
                             if (sizeof(TU) == sizeof(double))
-                                rc = pivot2x2_x2(pk, pmask, (double)H[pa + INNER_LD * pa].x,
-                                                 (double)H[pb + INNER_LD * pb].x, (double)hab.x,
-                                                 (double)hab.y, (double)S[pa + INNER_LD * pa].x,
-                                                 (double)S[pb + INNER_LD * pb].x, (double)sab.x,
-                                                 (double)sab.y, a.tol, a.crit_mode, zd, &big);
+                                rc = pivot2x2_x2<TU>(pk, pmask, H[pa + INNER_LD * pa].x, H[pb + INNER_LD * pb].x,
+                                                     hab.x, hab.y, S[pa + INNER_LD * pa].x,
+                                                     S[pb + INNER_LD * pb].x, sab.x, sab.y, a.tol, a.crit_mode,
+                                                     zrow, &big);
                             else
-                                rc = pivot2x2_fast_x2(pk, pmask, (double)H[pa + INNER_LD * pa].x,
-                                                      (double)H[pb + INNER_LD * pb].x, (double)hab.x,
-                                                      (double)hab.y, (double)S[pa + INNER_LD * pa].x,
-                                                      (double)S[pb + INNER_LD * pb].x, (double)sab.x,
-                                                      (double)sab.y, a.tol, a.crit_mode, zd, &big);
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) zl[q] = (TU)zd[q];
+                                rc = pivot2x2_fast_x2<TU>(pk, pmask, H[pa + INNER_LD * pa].x,
+                                                          H[pb + INNER_LD * pb].x, hab.x, hab.y,
+                                                          S[pa + INNER_LD * pa].x, S[pb + INNER_LD * pb].x,
+                                                          sab.x, sab.y, a.tol, a.crit_mode, zrow, &big);
                         } else {                        // complex64 sweeps, FP32 parameters
                             rc = pivot2x2<TU>(H[pa + INNER_LD * pa].x, H[pb + INNER_LD * pb].x, hab.x,
                                               hab.y, S[pa + INNER_LD * pa].x, S[pb + INNER_LD * pb].x,
@@ -206,6 +206,10 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                     // dependent at their rounding level alone; the FP64 sweeps
                     // that follow decide about rank deficiency
                     if (rc == PIV_ERR_RANK && sizeof(TU) == sizeof(float)) rc = PIV_NONE;
+                    if (paired && rc == PIV_TRANSFORM) {   // each lane stores its row of Z'
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) zu[l][4 * pk + q] = (TU)zrow[q];
+                    }
                     if (pk != 0) continue;                  // the pair's second lane
                     if (rc < 0) {
                         atomicOr(&s_err, rc == PIV_ERR_RANK ? DEVERR_RANK : DEVERR_NONFINITE);
@@ -213,8 +217,10 @@ __device__ __forceinline__ void inner_body(const typename cplx<TP>::t *__restric
                     }
                     tr[l] = rc == PIV_TRANSFORM;
                     if (rc == PIV_TRANSFORM) {
+                        if (!paired) {
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) zu[l][q] = zl[q];
+                            for (int q = 0; q < 8; ++q) zu[l][q] = zl[q];
+                        }
                         my_all += 1;
                         my_big += big;
                         step_all += 1;

@@ -156,30 +156,46 @@ __device__ __forceinline__ int pivot2x2(T hpp, T hqq, T hpq_re, T hpq_im, T spp,
 // The partner lane's value (lanes 2i, 2i+1 of the mask m).
 __device__ __forceinline__ double pswap(double v, unsigned m) { return __shfl_xor_sync(m, v, 1); }
 
+// The input tests of pivot2x2 on a lane pair: each lane tests the four
+// inputs it owns (s_pp or s_qq first: PIV_ERR_RANK before
+// PIV_ERR_NONFINITE), in the inputs' own precision; 0 if both pass.
+template <typename TI>
+__device__ __forceinline__ int pair_checks(unsigned m, TI s_own, TI h_own, TI hpq_own, TI spq_own)
+{
+    const int rank = !(s_own > TI(0));
+    const int fin = isfinite(s_own) && isfinite(h_own) && isfinite(hpq_own) && isfinite(spq_own);
+    const int bits = rank | (fin ? 0 : 2);
+    const int both = bits | __shfl_xor_sync(m, bits, 1);
+    return (both & 1) ? PIV_ERR_RANK : (both & 2) ? PIV_ERR_NONFINITE : 0;
+}
+
 // pivot2x2<double> on two lanes (k = 0, 1 of a lane pair; m = the pair's
 // mask), for the FP64 sweeps: every value is formed by the same operations
 // as in pivot2x2, in the lane that owns it (lane 0: the p side, real parts,
 // phi; lane 1: the q side, imaginary parts, psi), and the two lanes swap by
 // shuffles.  The chain holds 10 divisions and 7 square roots instead of 17
 // and 11 (an FP64 warp instruction occupies the FP64 pipe for the same time
-// whatever its active lanes).  Both lanes return the same code, *big, z.
-__device__ __forceinline__ int pivot2x2_x2(int k, unsigned m, double hpp, double hqq, double hpq_re,
-                                           double hpq_im, double spp, double sqq, double spq_re,
-                                           double spq_im, double tol, int crit_mode, double z[8], int *big)
+// whatever its active lanes).  Each lane reads and tests the four inputs it
+// owns (in their own precision TI) and returns its own row of Z',
+// zrow[0..3] = (re, im) of z_k1, z_k2 (lane 0: z11, z12; lane 1: z21, z22);
+// both lanes return the same code and *big.
+template <typename TI>
+__device__ __forceinline__ int pivot2x2_x2(int k, unsigned m, TI hpp, TI hqq, TI hpq_re, TI hpq_im, TI spp,
+                                           TI sqq, TI spq_re, TI spq_im, double tol, int crit_mode,
+                                           double zrow[4], int *big)
 {
     const double one = 1.0, zero = 0.0, half = 0.5;
     *big = 0;
-    if (!(spp > zero) || !(sqq > zero)) return PIV_ERR_RANK;
-    if (!isfinite(hpp) || !isfinite(hqq) || !isfinite(hpq_re) || !isfinite(hpq_im) ||
-        !isfinite(spp) || !isfinite(sqq) || !isfinite(spq_re) || !isfinite(spq_im))
-        return PIV_ERR_NONFINITE;
+    const TI s_own = k ? sqq : spp, h_own = k ? hqq : hpp;
+    const TI hpq_own = k ? hpq_im : hpq_re, spq_own = k ? spq_im : spq_re;
+    if (const int bad = pair_checks<TI>(m, s_own, h_own, hpq_own, spq_own)) return bad;
     // Section 6.1.1
-    const double d = one / sqrt(k ? sqq : spp), d_o = pswap(d, m);
+    const double d = one / sqrt((double)s_own), d_o = pswap(d, m);
     const double dp = k ? d_o : d, dq = k ? d : d_o;
     const double dpq = dp * dq;
-    const double hh = mul_rn(mul_rn(k ? hqq : hpp, d), d), hh_o = pswap(hh, m);
+    const double hh = mul_rn(mul_rn((double)h_own, d), d), hh_o = pswap(hh, m);
     const double h11 = k ? hh_o : hh, h22 = k ? hh : hh_o;
-    const double ho = (k ? hpq_im : hpq_re) * dpq, so = (k ? spq_im : spq_re) * dpq;
+    const double ho = (double)hpq_own * dpq, so = (double)spq_own * dpq;
     const double ho_o = pswap(ho, m), so_o = pswap(so, m);
     const double h12r = k ? ho_o : ho, h12i = k ? ho : ho_o;
     const double s12r = k ? so_o : so, s12i = k ? so : so_o;
@@ -257,10 +273,7 @@ __device__ __forceinline__ int pivot2x2_x2(int k, unsigned m, double hpp, double
         *big = !(cphi == one && cpsi == one);               // Section 6.1.7
     }
     // Z' = D0^ Z^: lane 0 scales the first row by dp, lane 1 the second by dq
-    zr0 = d * zr0; zi0 = d * zi0; zr1 = d * zr1; zi1 = d * zi1;
-    const double o0 = pswap(zr0, m), o1 = pswap(zi0, m), o2 = pswap(zr1, m), o3 = pswap(zi1, m);
-    if (k == 0) { z[0] = zr0; z[1] = zi0; z[2] = zr1; z[3] = zi1; z[4] = o0; z[5] = o1; z[6] = o2; z[7] = o3; }
-    else { z[0] = o0; z[1] = o1; z[2] = o2; z[3] = o3; z[4] = zr0; z[5] = zi0; z[6] = zr1; z[7] = zi1; }
+    zrow[0] = d * zr0; zrow[1] = d * zi0; zrow[2] = d * zr1; zrow[3] = d * zi1;
     return PIV_TRANSFORM;
 }
 
@@ -279,24 +292,25 @@ __device__ __forceinline__ int pivot2x2_x2(int k, unsigned m, double hpp, double
 // lane 0 computes one member, lane 1 the other, and the two swap by a
 // shuffle (measured on the one-lane form of the same formulas: eight
 // reciprocal square roots and about twice the products on the critical
-// path).  Both lanes return the same code, *big and z[0..7].
-__device__ __forceinline__ int pivot2x2_fast_x2(int k, unsigned m, double hpp, double hqq, double hpq_re,
-                                                double hpq_im, double spp, double sqq, double spq_re,
-                                                double spq_im, double tol, int crit_mode, double z[8],
-                                                int *big)
+// path).  Inputs and outputs as pivot2x2_x2: each lane tests and converts
+// its own four inputs and returns its own row of Z' in zrow[0..3]; both lanes
+// return the same code and *big.
+template <typename TI>
+__device__ __forceinline__ int pivot2x2_fast_x2(int k, unsigned m, TI hpp, TI hqq, TI hpq_re, TI hpq_im,
+                                                TI spp, TI sqq, TI spq_re, TI spq_im, double tol,
+                                                int crit_mode, double zrow[4], int *big)
 {
     *big = 0;
-    if (!(spp > 0.0) || !(sqq > 0.0)) return PIV_ERR_RANK;
-    if (!isfinite(hpp) || !isfinite(hqq) || !isfinite(hpq_re) || !isfinite(hpq_im) ||
-        !isfinite(spp) || !isfinite(sqq) || !isfinite(spq_re) || !isfinite(spq_im))
-        return PIV_ERR_NONFINITE;
+    const TI s_own = k ? sqq : spp, h_own = k ? hqq : hpp;
+    const TI hpq_own = k ? hpq_im : hpq_re, spq_own = k ? spq_im : spq_re;
+    if (const int bad = pair_checks<TI>(m, s_own, h_own, hpq_own, spq_own)) return bad;
     // Section 6.1.1 (lane 0: p, lane 1: q)
-    const double d = rsqrt(k ? sqq : spp), d_o = pswap(d, m);
+    const double d = rsqrt((double)s_own), d_o = pswap(d, m);
     const double dp = k ? d_o : d, dq = k ? d : d_o;
     const double dpq = dp * dq;
-    const double hh = (k ? hqq : hpp) * d * d, hh_o = pswap(hh, m);
+    const double hh = (double)h_own * d * d, hh_o = pswap(hh, m);
     const double h11 = k ? hh_o : hh, h22 = k ? hh : hh_o;
-    const double ho = (k ? hpq_im : hpq_re) * dpq, so = (k ? spq_im : spq_re) * dpq;
+    const double ho = (double)hpq_own * dpq, so = (double)spq_own * dpq;
     const double ho_o = pswap(ho, m), so_o = pswap(so, m);
     const double h12r = k ? ho_o : ho, h12i = k ? ho : ho_o;
     const double s12r = k ? so_o : so, s12i = k ? so : so_o;
@@ -370,10 +384,7 @@ __device__ __forceinline__ int pivot2x2_fast_x2(int k, unsigned m, double hpp, d
         *big = own | __shfl_xor_sync(m, own, 1);
     }
     // Z' = D0^ Z^: lane 0 scales the first row by dp, lane 1 the second by dq
-    zr0 *= d; zi0 *= d; zr1 *= d; zi1 *= d;
-    const double o0 = pswap(zr0, m), o1 = pswap(zi0, m), o2 = pswap(zr1, m), o3 = pswap(zi1, m);
-    if (k == 0) { z[0] = zr0; z[1] = zi0; z[2] = zr1; z[3] = zi1; z[4] = o0; z[5] = o1; z[6] = o2; z[7] = o3; }
-    else { z[0] = o0; z[1] = o1; z[2] = o2; z[3] = o3; z[4] = zr0; z[5] = zi0; z[6] = zr1; z[7] = zi1; }
+    zrow[0] = zr0 * d; zrow[1] = zi0 * d; zrow[2] = zr1 * d; zrow[3] = zi1 * d;
     return PIV_TRANSFORM;
 }
 
