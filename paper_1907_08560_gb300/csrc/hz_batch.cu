@@ -187,7 +187,7 @@ __global__ void round_finish_batched(const BPencil *__restrict__ P, const BState
 //
 // Mixed schedule (the rules of the single solve): a complex64 round ends when
 // its big count levels off (more than 0.8 of the previous sweep's and below
-// 1 % of the pivots), when no pivot rotated, or at the complex64 sweep
+// 10 % of the pivots), when no pivot rotated, or at the complex64 sweep
 // budget; the pencil then waits one tick for the product W Z'_low and either
 // starts another round (at most two) or continues with FP64 sweeps.  The
 // pencils waiting for a product are listed for the next tick.
@@ -227,7 +227,7 @@ __global__ void control_batched(const BPencil *__restrict__ P, BState *__restric
                     st.sweeps_low += 1;
                     st.round_sweeps += 1;
                     const bool plateau = st.round_sweeps >= 2 && (double)big > 0.8 * (double)st.prev_big &&
-                                         (double)big < 0.01 * p.pivots_per_sweep;
+                                         (double)big < 0.1 * p.pivots_per_sweep;
                     st.prev_big = big;
                     const bool budget = st.sweeps_low >= mixed_max_sweeps;
                     if (all == 0 || plateau || budget) {

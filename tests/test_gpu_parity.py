@@ -248,9 +248,9 @@ def test_not_converged_status_still_writes_outputs(gh):
 def test_mixed_precision_schedule(gh):
     F, J, G = P.single_pencil_64()
     ref = oracle.solve(F, G, J, method="blocked", w=8)
-    # at n = 64 the complex64 round runs to its 24-sweep budget (its rounding
-    # floor stays above 1 % of the pivots) and the FP64 sweeps then take 5-8
-    # more, near the default C_max of 30: the limit is raised
+    # at n = 64 the complex64 rounds and the FP64 sweeps that follow take
+    # 27-32 sweeps (FP64 alone: 21), near the default C_max of 30: the limit
+    # is raised
     gpu = gpu_solve(gh, F, G, J, block_width=8, precision=gh.GHSVD_PRECISION_MIXED, max_sweeps=40)
     assert gpu["status"] == 0
     assert gpu["stats"]["sweeps_low"] >= 1
