@@ -277,9 +277,10 @@ void ghsvd_destroy(ghsvd_t h);
  * of ghsvd_solve on its own clock: complex64 rounds (mixed_max_sweeps,
  * mixed_param32 apply; the complex64 Grams and updates run on the CUDA
  * cores, mixed_tc is not used), each ended by the FP64 product W Z'_low in
- * the next tick, then FP64 sweeps to the stopping rule; pencils given a V0
- * run the FP64 schedule.  ghsvd_stats.sweeps_low and rounds_low are the sums
- * over the pencils.  delta_update is not used by batched solves.
+ * the next tick, then FP64 sweeps to the stopping rule; a pencil given a V0
+ * starts its first round from (F V0, G V0).  ghsvd_stats.sweeps_low and
+ * rounds_low are the sums over the pencils.  delta_update is not used by
+ * batched solves.
  * Returns GHSVD_OK when every pencil converged, otherwise the status of the
  * first pencil that failed (or GHSVD_ERR_NOT_CONVERGED).
  */

@@ -368,8 +368,8 @@ Plan make_plan(int batch, const int64_t *m, const int64_t *p, const int64_t *n, 
         q.oErr = carve(8);
         q.oLam = carve(8LL * q.n); q.oGsc = carve(8LL * q.n); q.oVn = carve(8LL * q.n);
         q.oGc = carve(8LL * q.n); q.oKap = carve(8); q.oRank = carve(4LL * q.n);
-        // the mixed schedule for every pencil without a starting basis
-        q.mixed = mixed && !(with_v0 && V0[i]) && q.n >= 2;
+        // the mixed schedule for every pencil (a starting basis is applied first)
+        q.mixed = mixed && q.n >= 2;
         q.oTmp = (with_v0 || q.mixed) ? carve(16LL * q.Mt * q.n) : -1;
         q.oW32 = q.mixed ? carve(8LL * q.Mt * q.n) : -1;
         pl.gram_work += q.npairs * cpp;
@@ -498,10 +498,6 @@ static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, con
         BT_TRY(hz::launch_copyin(d.W, false, q.Mt, q.m, q.p, q.n, q.m_pad, q.p_pad, q.n_pad, F[i],
                                  ldf[i], G[i], ldg[i], nullptr, 0, d.err, st));
         BT_TRY(hz::launch_gnorm(d.W, q.Mt, q.m_pad, q.p_pad, q.n, (double *)(base + q.oGc), st));
-        if (q.mixed) {      // the first complex64 round starts from fl32(W) and Z' = I
-            BT_TRY(hz::launch_convert(d.W32, true, d.W, q.Mt * q.n, st));
-            BT_TRY(hz::launch_eye32(d.W32, q.Mt, q.m_pad + q.p_pad, q.n, q.n_pad, st));
-        }
     }
     // warm starts: (F V0, G V0) with Z' = V0 for every pencil that has a V0,
     // as one batched FP64 product and one batched copy
@@ -553,6 +549,14 @@ static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, con
                 *ms_v0 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tv).count();
             }
         }
+    }
+    // the first complex64 round of a pencil on the mixed schedule starts from
+    // fl32(W) (after its starting basis, if any) with Z' = I
+    for (int i = 0; i < batch; ++i) {
+        const PlanP &q = pl.pp[i];
+        if (!q.mixed) continue;
+        BT_TRY(hz::launch_convert(hp[i].W32, true, hp[i].W, q.Mt * q.n, st));
+        BT_TRY(hz::launch_eye32(hp[i].W32, q.Mt, q.m_pad + q.p_pad, q.n, q.n_pad, st));
     }
     for (int i = 0; i < batch; ++i) {
         const PlanP &q = pl.pp[i];

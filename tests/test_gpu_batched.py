@@ -169,31 +169,61 @@ def test_batched_mixed_schedule_matches_oracle_per_pencil(gh, w, param32):
         assert np.max(np.abs(GV.conj().T @ GV - np.eye(F.shape[1]))) < 1e-8
 
 
-def test_batched_mixed_with_starting_basis_keeps_fp64_for_that_pencil(gh):
-    # a pencil given a starting Z' runs the FP64 schedule; the others the mixed one
+def test_batched_mixed_with_starting_basis(gh):
+    # a pencil given a starting Z' runs the mixed schedule from (F V0, G V0),
+    # as a single solve does; the others from (F, G)
     batch = small_batch()[:3]
     n0 = batch[0][0].shape[1]
-    V0 = gh.colmajor(torch.eye(n0, dtype=torch.complex128)).cuda()
-    s = gh.Solver(0, block_width=8, precision=gh.GHSVD_PRECISION_MIXED)
-    lams, _, sweeps, statuses, st = s.solve_batched(
+    rng = np.random.default_rng(77)
+    V0h = np.eye(n0) + 0.05 * (rng.standard_normal((n0, n0)) + 1j * rng.standard_normal((n0, n0)))
+    V0 = gh.colmajor(torch.from_numpy(V0h)).cuda()
+    s = gh.Solver(0, block_width=8, precision=gh.GHSVD_PRECISION_MIXED, max_sweeps=60)
+    lams, Vs, sweeps, statuses, st = s.solve_batched(
         [dev(gh, F) for F, _, _ in batch], [dev(gh, G) for _, _, G in batch],
-        [torch.from_numpy(J).cuda() for _, J, _ in batch], want_vectors=False,
-        V0s=[V0, None, None])
-    assert st == gh.GHSVD_OK
-    for (F, J, G), lam in zip(batch, lams):
+        [torch.from_numpy(J).cuda() for _, J, _ in batch], V0s=[V0, None, None])
+    assert st == gh.GHSVD_OK and all(x == 0 for x in statuses)
+    assert s.stats()["rounds_low"] >= len(batch)
+    for (F, J, G), lam, V in zip(batch, lams, Vs):
         ref = oracle.solve(F, G, J, method="blocked", w=8)
         tol = eig_tol_vec(F, G, J, ref["lam"], ref["F"])
         assert np.all(rel_err(lam.cpu().numpy(), ref["lam"]) < tol)
-    # the pencil with the starting basis runs exactly as in an FP64 batched
-    # solve of the same pencils (same plan, same arithmetic): bitwise equal
-    one = gh.Solver(0, block_width=8)
-    l1, _, sw1, _, _ = one.solve_batched(
+        GV = G @ V.cpu().numpy()
+        assert np.max(np.abs(GV.conj().T @ GV - np.eye(F.shape[1]))) < 1e-8
+
+
+def test_batched_mixed_failure_stays_in_its_pencil(gh):
+    # a rank-deficient G in one pencil: its complex64 rounds pass over the
+    # dependent pivots and its FP64 sweeps report it; the others converge
+    batch = small_batch()[:3]
+    F1, J1, G1 = batch[1]
+    G1 = G1.copy()
+    G1[:, 5] = G1[:, 9]
+    batch[1] = (F1, J1, G1)
+    s = gh.Solver(0, block_width=8, precision=gh.GHSVD_PRECISION_MIXED, max_sweeps=60)
+    lams, _, _, statuses, st = s.solve_batched(
         [dev(gh, F) for F, _, _ in batch], [dev(gh, G) for _, _, G in batch],
-        [torch.from_numpy(J).cuda() for _, J, _ in batch], want_vectors=False,
-        V0s=[V0, None, None])
-    assert sweeps[0] == sw1[0]
-    assert torch.equal(lams[0], l1[0])
-    assert s.stats()["rounds_low"] >= 2 and one.stats()["rounds_low"] == 0
+        [torch.from_numpy(J).cuda() for _, J, _ in batch], want_vectors=False)
+    assert statuses[1] == gh.GHSVD_ERR_RANK_DEFICIENT
+    assert statuses[0] == 0 and statuses[2] == 0
+    assert st == gh.GHSVD_ERR_RANK_DEFICIENT
+    for i in (0, 2):
+        F, J, G = batch[i]
+        ref = oracle.solve(F, G, J, method="blocked", w=8)
+        tol = eig_tol_vec(F, G, J, ref["lam"], ref["F"])
+        assert np.all(rel_err(lams[i].cpu().numpy(), ref["lam"]) < tol)
+
+
+def test_batched_mixed_sweep_limit(gh):
+    # C_max counts the complex64 sweeps too: a limit below the schedule's
+    # needs stops every pencil with NOT_CONVERGED and its sweep count at C_max
+    batch = small_batch()[:2]
+    s = gh.Solver(0, block_width=8, precision=gh.GHSVD_PRECISION_MIXED, max_sweeps=5)
+    lams, _, sweeps, statuses, st = s.solve_batched(
+        [dev(gh, F) for F, _, _ in batch], [dev(gh, G) for _, _, G in batch],
+        [torch.from_numpy(J).cuda() for _, J, _ in batch], want_vectors=False)
+    assert st == gh.GHSVD_ERR_NOT_CONVERGED
+    assert all(x == gh.GHSVD_ERR_NOT_CONVERGED for x in statuses)
+    assert all(sw == 5 for sw in sweeps)
 
 
 def test_batched_mixed_kpoint_pencils_match_oracle_golden(gh):
