@@ -242,3 +242,23 @@ def test_batched_mixed_kpoint_pencils_match_oracle_golden(gh):
     assert stt["sweeps_low"] >= 3
     for g, lam in zip(goldens, lams):
         assert golden_ratio(lam.cpu().numpy(), g) < 1.0, g["name"]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_deterministic(gh, precision):
+    batch = small_batch()[:4]
+    outs = []
+    for _ in range(2):
+        s = gh.Solver(0, block_width=16, precision=precision, max_sweeps=60)
+        lams, Vs, sweeps, statuses, st = s.solve_batched(
+            [dev(gh, F) for F, _, _ in batch], [dev(gh, G) for _, _, G in batch],
+            [torch.from_numpy(J).cuda() for _, J, _ in batch])
+        assert st == gh.GHSVD_OK
+        outs.append((lams, Vs, sweeps))
+        s.close()
+    (la, Va, sa), (lb, Vb, sb) = outs
+    assert sa == sb
+    for x, y in zip(la, lb):
+        assert torch.equal(x, y)
+    for x, y in zip(Va, Vb):
+        assert torch.equal(x, y)

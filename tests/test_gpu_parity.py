@@ -160,10 +160,16 @@ def test_sorted_output(gh):
     assert np.max(np.abs(GV.conj().T @ GV - np.eye(64))) < 1e-6
 
 
-def test_deterministic(gh):
+@pytest.mark.parametrize("opts", [dict(block_width=8), dict(block_width=32, precision=1, max_sweeps=60),
+                                  dict(block_width=32, precision=1, mixed_tc=0, max_sweeps=60)])
+def test_deterministic(gh, opts):
+    # the same inputs give the same bits: FP64 sweeps, and the mixed schedule
+    # with its complex64 Grams and updates on the tensor cores or the CUDA
+    # cores (every reduction has a fixed order)
     F, J, G = P.single_pencil_64()
-    a = gpu_solve(gh, F, G, J, block_width=8)
-    b = gpu_solve(gh, F, G, J, block_width=8)
+    a = gpu_solve(gh, F, G, J, **opts)
+    b = gpu_solve(gh, F, G, J, **opts)
+    assert a["status"] == 0 and a["sweeps"] == b["sweeps"]
     assert np.array_equal(a["lam"], b["lam"]) and np.array_equal(a["V"], b["V"])
 
 
