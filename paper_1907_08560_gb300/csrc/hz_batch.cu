@@ -4,14 +4,17 @@
 //
 // Each pencil keeps its own working buffers, schedule (block partition and
 // round-robin tables, Section 6.3, 6.4.1), transformation counters and state
-// (current outer step, sweep, active flag).  A tick is four launches: the
-// Gram, inner and update kernels over the work items of every pencil (CTAs of
-// inactive pencils return at once), and a control kernel that advances each
-// pencil's step and, at the end of its sweep, applies the stopping rule of
-// Section 6.1.7 to that pencil's own counters.  The whole iteration is one
-// launch of a CUDA graph whose conditional while node repeats the tick: the
-// control kernel sets the loop condition on the device, and the host waits
-// once, when no pencil is active any more.
+// (current outer step, sweep, active flag, phase).  A tick is the Gram, inner
+// and update kernels over the work items of every pencil (CTAs of inactive
+// pencils return at once), and a control kernel that advances each pencil's
+// step and, at the end of its sweep, applies the stopping rule of Section
+// 6.1.7 to that pencil's own counters.  With the mixed schedule a tick also
+// holds the complex64 instances of the three step kernels (each pencil runs
+// the instance of its phase) and, first, the FP64 products W Z'_low of the
+// pencils whose complex64 round ended in the previous tick.  The whole
+// iteration is one launch of a CUDA graph whose conditional while node
+// repeats the tick: the control kernel sets the loop condition on the
+// device, and the host waits once, when no pencil is active any more.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
