@@ -552,7 +552,7 @@ def main():
     torch.cuda.synchronize()
 
     acc = dict(ms_update=0.0, launches_update=0, ms_gram=0.0, launches_gram=0, ms_inner=0.0,
-               launches_inner=0, kernel_launches=0, sweeps=0, pairs_delta=0, pairs_fp64=0)
+               launches_inner=0, kernel_launches=0, sweeps=0, pairs_delta=0, pairs_fp64=0, pairs_df=0)
     clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
@@ -585,20 +585,27 @@ def main():
     sizes = dict(n=N, m=M, p=P, w=W_BLOCK)
     achieved = update_flops_per_launch(**sizes) / (upd_ms * 1e-3) / 1e12
     # `achieved` counts 8 real flops per complex MAC (the algorithmic count);
-    # the kernel's three-multiplication form executes 3 FMAs (6 flops) per
-    # complex MAC, so `frac` can exceed 1 and `executed_frac` is the FP64
-    # pipe's share of the work actually issued
+    # the FP64 kernel's three-multiplication form executes 3 FMAs (6 flops)
+    # per complex MAC, and the pairs routed to the delta forms run on the FP32
+    # pipe, so `frac` can exceed 1; `executed_frac` is the FP64 pipe's share
+    # of the FP64 FMAs actually issued (the FP64-product pairs only)
+    routed = acc["pairs_delta"] + acc["pairs_fp64"] + acc["pairs_df"]
+    fp64_share = acc["pairs_fp64"] / routed if routed else 1.0
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops if peak_tflops else None,
                 "executed_flops_per_complex_mac": 6,
-                "executed_frac": 0.75 * achieved / peak_tflops if peak_tflops else None,
+                "fp64_product_pair_share": fp64_share,
+                "executed_frac": 0.75 * fp64_share * achieved / peak_tflops if peak_tflops else None,
                 "traffic": traffic_per_launch() if N == 2048 else None,
                 "kernel": "update_kernel<double,double>",
                 "update_phase": ("the update phase of a step: the FP64 product (update_kernel) for "
-                                 "pairs with a large transformation, the delta form "
-                                 "(update_delta64_kernel) for pairs whose Z^ - I <= 2^-29, and the "
-                                 "routing kernel; timed together with CUDA events"),
+                                 "pairs with a large transformation, the delta form X + X(Z^ - I) "
+                                 "with an FP32 product (update_delta64_kernel) for pairs whose "
+                                 "Z^ - I <= 2^-29 and with a double-float product "
+                                 "(update_df64_kernel) for Z^ - I <= 2^-11, and the routing "
+                                 "kernel; timed together with CUDA events"),
                 "pairs_delta_form": acc["pairs_delta"], "pairs_fp64_product": acc["pairs_fp64"],
+                "pairs_double_float": acc["pairs_df"],
                 "peak_source": "FP64 DFMA measured live on this GPU (libhzpeak)",
                 "gram": {"achieved": gram_flops_per_launch(**sizes) / (gram_ms * 1e-3) / 1e12,
                          "ms_per_launch": gram_ms},

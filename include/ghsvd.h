@@ -131,12 +131,15 @@ typedef struct {
                             The 2x2 parameters, J-norms and stopping test are
                             FP64 either way.                                  */
     int delta_update;    /* FP64 sweeps: 1 (default) updates every pair whose
-                            Z^ - I has all entries <= 2^-29 in the delta form
-                            X + X (Z^ - I), the product from FP32 roundings by
-                            FP32 FMAs, the sum in FP64 (error bound about
-                            2^-47 sum_l |x_il| per entry, the size of the FP64
-                            product's bound for rows of comparable entries); the
-                            other pairs, and every pair with 0, by the FP64
+                            Z^ - I is small in the delta form X + X (Z^ - I),
+                            the sum in FP64: with all entries <= 2^-29 the
+                            product from FP32 roundings by FP32 FMAs (error
+                            bound about 2^-47 sum_l |x_il| per entry; typical
+                            error that of the FP64 product), with all entries
+                            <= 2^-11 in double-float arithmetic (FP32 pairs, 48
+                            significant bits; bound about 2^-52 sum_l |x_il|,
+                            typical error far below the FP64 product's).
+                            The other pairs, and every pair with 0, by the FP64
                             product                                           */
 } ghsvd_opts;
 
@@ -167,6 +170,9 @@ typedef struct {
                                       taken in the delta form, over the solve  */
     long long pairs_fp64;          /* with opts.delta_update: FP64 pair updates
                                       by the FP64 product, over the solve      */
+    long long pairs_df;            /* with opts.delta_update: FP64 pair updates
+                                      in the delta form with the product in
+                                      double-float arithmetic, over the solve  */
 } ghsvd_stats;
 
 /* Fill *opts with the defaults listed above. */

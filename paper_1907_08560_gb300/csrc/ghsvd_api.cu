@@ -58,11 +58,11 @@ struct ghsvd_ctx {
     void *partial = nullptr;            // Gram partials (FP64 or FP32 pairs)
     double2 *zhat = nullptr;            // [pairs][KKMAX^2] accumulated block transforms
     int *pair_flag = nullptr;           // [pairs]
-    int *route = nullptr;               // [2][pairs]: tensor-core / CUDA-core update of a pair
+    int *route = nullptr;               // [3][pairs]: the update route of each pair
     int *slotcol = nullptr;             // [steps][pairs][kk]
     int8_t *Jrow = nullptr;             // [m_pad]
     int8_t *Jdev = nullptr;             // [m] staging of a host J
-    unsigned long long *counters = nullptr;   // [2]
+    unsigned long long *counters = nullptr;   // [5]: all, big, delta, FP64, double-float pairs
     int *err = nullptr;                 // [2]: device error flags, bad J
     double *lam_tmp = nullptr, *gscale = nullptr;
     double *vnorm2 = nullptr, *gcol2 = nullptr, *kappa = nullptr;
@@ -236,7 +236,7 @@ ghsvd_status ghsvd_create(ghsvd_t *out, int device, const ghsvd_opts *opts)
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = hz::setup_kernels();
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_counters, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_counters, 5 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_err, 2 * sizeof(int));
     cudaSetDevice(prev);
     if (e != cudaSuccess) {
@@ -320,7 +320,7 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
         h->zhat = nullptr; h->pair_flag = nullptr; h->route = nullptr;
         CUDA_TRY(cudaMalloc((void **)&h->zhat, sizeof(double2) * std::max(npairs, 1) * hz::KKMAX * hz::KKMAX));
         CUDA_TRY(cudaMalloc((void **)&h->pair_flag, sizeof(int) * std::max(npairs, 1)));
-        CUDA_TRY(cudaMalloc((void **)&h->route, 2 * sizeof(int) * std::max(npairs, 1)));
+        CUDA_TRY(cudaMalloc((void **)&h->route, 3 * sizeof(int) * std::max(npairs, 1)));
         h->cap_pairs = std::max(npairs, 1);
     }
     cap = (long long)h->cap_steps;
@@ -353,7 +353,7 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
     if (!h->counters) {
         // all, big transformations of the sweep; FP64 pair updates in the
         // delta form and by the FP64 product
-        CUDA_TRY(cudaMalloc((void **)&h->counters, 4 * sizeof(unsigned long long)));
+        CUDA_TRY(cudaMalloc((void **)&h->counters, 5 * sizeof(unsigned long long)));
         CUDA_TRY(cudaMalloc((void **)&h->err, 2 * sizeof(int)));
         CUDA_TRY(cudaMalloc((void **)&h->kappa, sizeof(double)));
     }
@@ -483,7 +483,7 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
             ia.tol = single ? tol32 : tol64;
             ia.cpp = tcs ? chunks_h_tc + chunks_s_tc : chunks_h + chunks_s;
             ia.chunks_h = tcs ? chunks_h_tc : chunks_h;
-            CUDA_TRY(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned long long), st));
+            CUDA_TRY(cudaMemsetAsync(h->counters, 0, 5 * sizeof(unsigned long long), st));
             const bool timed = o.timing != 0;
             const bool delta = !single && o.delta_update;
             if (timed) CUDA_TRY(h->timer.reserve(6 * nsteps));
@@ -512,11 +512,14 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
                     CUDA_TRY(hz::launch_update_tc(Wc, sa, n, h->zhat, tcf, h->err, h->num_sms, st));
                     CUDA_TRY(hz::launch_update(Wc, true, sa, h->zhat, ccf, st));
                 } else if (delta) {
-                    // pairs whose Z^ - I is tiny in the delta form (hz_delta.cu),
-                    // the others by the FP64 product
-                    int *df = h->route, *ff = h->route + npairs;
-                    CUDA_TRY(hz::launch_route64(h->zhat, h->pair_flag, kk, npairs, df, ff, h->counters + 2, st));
-                    CUDA_TRY(hz::launch_update_delta64(h->W, sa, h->zhat, df, st));
+                    // pairs whose Z^ - I is small in the delta form (FP32 or
+                    // double-float product, hz_delta.cu), the others by the
+                    // FP64 product
+                    int *dl = h->route, *ff = h->route + npairs, *dd = h->route + 2 * npairs;
+                    CUDA_TRY(hz::launch_route64(h->zhat, h->pair_flag, kk, npairs, dl, dd, ff, h->counters + 2,
+                                                st));
+                    CUDA_TRY(hz::launch_update_delta64(h->W, sa, h->zhat, dl, st));
+                    CUDA_TRY(hz::launch_update_df64(h->W, sa, h->zhat, dd, st));
                     CUDA_TRY(hz::launch_update(Wc, false, sa, h->zhat, ff, st));
                 } else {
                     CUDA_TRY(hz::launch_update(Wc, single, sa, h->zhat, h->pair_flag, st));
@@ -526,8 +529,8 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
             h->stats.launches_gram += nsteps;
             h->stats.launches_inner += nsteps;
             h->stats.launches_update += nsteps;
-            h->stats.kernel_launches += (tcs || delta ? 5LL : 3LL) * nsteps;
-            CUDA_TRY(cudaMemcpyAsync(h->h_counters, h->counters, 4 * sizeof(unsigned long long),
+            h->stats.kernel_launches += (delta ? 6LL : tcs ? 5LL : 3LL) * nsteps;
+            CUDA_TRY(cudaMemcpyAsync(h->h_counters, h->counters, 5 * sizeof(unsigned long long),
                                      cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaMemcpyAsync(h->h_err, h->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaStreamSynchronize(st));
@@ -552,6 +555,7 @@ static ghsvd_status solve_impl(ghsvd_t h, int64_t m64, int64_t p64, int64_t n64,
             if (delta) {
                 h->stats.pairs_delta += (long long)h->h_counters[2];
                 h->stats.pairs_fp64 += (long long)h->h_counters[3];
+                h->stats.pairs_df += (long long)h->h_counters[4];
             }
             if (h->h_err[0] & hz::DEVERR_TIMEOUT) { status = GHSVD_ERR_CUDA; break; }
             if (h->h_err[0] & hz::DEVERR_RANK) { status = GHSVD_ERR_RANK_DEFICIENT; break; }

@@ -157,12 +157,16 @@ cudaError_t launch_update_tc(void *W32, const StepArgs &a, int n, const double2 
 cudaError_t launch_route(const double2 *zhat, const int *pair_flag, int kk, int npairs, int *tc_flag,
                          int *cc_flag, cudaStream_t s);
 
-// FP64 sweeps: the delta-form update of pairs whose Z^ - I is tiny
-// (hz_delta.cu).  delta_flag[p] = 1: pair p goes to launch_update_delta64;
-// full_flag[p] = 1: to launch_update (FP64 product); *count += delta pairs.
+// FP64 sweeps: the delta-form update of pairs whose Z^ - I is small
+// (hz_delta.cu).  delta_flag[p] = 1: pair p goes to launch_update_delta64
+// (FP32 product); df_flag[p] = 1: to launch_update_df64 (double-float
+// product); full_flag[p] = 1: to launch_update (FP64 product); count[0],
+// count[1], count[2] += the delta, FP64 and double-float pairs.
 cudaError_t delta64_setup();
 cudaError_t launch_route64(const double2 *zhat, const int *pair_flag, int kk, int npairs, int *delta_flag,
-                           int *full_flag, unsigned long long *count, cudaStream_t s);
+                           int *df_flag, int *full_flag, unsigned long long *count, cudaStream_t s);
+cudaError_t launch_update_df64(double2 *W, const StepArgs &a, const double2 *zhat, const int *df_flag,
+                               cudaStream_t s);
 cudaError_t launch_update_delta64(double2 *W, const StepArgs &a, const double2 *zhat, const int *delta_flag,
                                   cudaStream_t s);
 

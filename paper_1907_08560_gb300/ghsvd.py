@@ -57,7 +57,8 @@ class ghsvd_stats(ctypes.Structure):
                 ("n2x2", ctypes.c_int), ("sweeps_tc", ctypes.c_int),
                 ("batch_ticks", ctypes.c_longlong), ("batch_graph_launches", ctypes.c_int),
                 ("ms_v0", ctypes.c_double), ("pairs_delta", ctypes.c_longlong),
-                ("pairs_fp64", ctypes.c_longlong)]
+                ("pairs_fp64", ctypes.c_longlong),
+                ("pairs_df", ctypes.c_longlong)]
 
 
 class GhsvdError(RuntimeError):
@@ -560,7 +561,7 @@ def ghsvd_get_stats(h) -> dict:
                 rounds_low=st.rounds_low, ms_phase2=st.ms_phase2, n2x2=st.n2x2,
                 sweeps_tc=st.sweeps_tc, batch_ticks=st.batch_ticks,
                 batch_graph_launches=st.batch_graph_launches, ms_v0=st.ms_v0,
-                pairs_delta=st.pairs_delta, pairs_fp64=st.pairs_fp64)
+                pairs_delta=st.pairs_delta, pairs_fp64=st.pairs_fp64, pairs_df=st.pairs_df)
 
 
 def ghsvd_urv(F, J, G, n_plus: int | None = None, stream=None):
