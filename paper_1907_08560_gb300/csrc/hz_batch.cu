@@ -30,6 +30,7 @@
 #include "hz_gram.cuh"
 #include "hz_inner.cuh"
 #include "hz_update.cuh"
+#include "hz_delta.cuh"
 #include "hz_launch.h"
 
 namespace hz {
@@ -45,6 +46,7 @@ struct BPencil {
     double2 *partial;           // [npairs][cpp][KKMAX^2]
     double2 *zhat;              // [npairs][KKMAX^2]
     int *flag;                  // [npairs]
+    int *route;                 // [npairs]: FP64 update route (route_class) of this step
     unsigned long long *cnt;    // [2]: all, big of the current sweep
     int *err;                   // [2]
     int m_pad, p_pad, n_pad, n;
@@ -130,8 +132,38 @@ update_batched(const BPencil *__restrict__ P, const BState *__restrict__ S, cons
     const int r = st.step;
     using T2 = typename cplx<T>::t;
     T2 *Wt = sizeof(T) == 8 ? (T2 *)p.W : (T2 *)p.W32;
-    update_body<T, T>(Wt, p.ld, p.slot + ((long long)r * p.npairs + w.y) * p.kk, p.kk, (long long)w.z * UPD_R,
-                      (const T2 *)p.zhat + (long long)w.y * KKMAX * KKMAX, smraw);
+    const int *slot = p.slot + ((long long)r * p.npairs + w.y) * p.kk;
+    const long long row0 = (long long)w.z * UPD_R;
+    if constexpr (sizeof(T) == 8) {
+        // FP64 sweeps: the delta forms for pairs whose Z^ - I is small
+        const double2 *zp = p.zhat + (long long)w.y * KKMAX * KKMAX;
+        const int c = p.route[w.y];
+        if (c == 0) {
+            delta64_tile(p.W, p.ld, slot, p.kk, row0, zp, smraw);
+            return;
+        }
+        if (c == 1) {
+            df64_tile(p.W, p.ld, slot, p.kk, row0, zp, smraw);
+            __syncthreads();                    // the first half's shared buffers are free
+            df64_tile(p.W, p.ld, slot, p.kk, row0 + DF_R, zp, smraw);
+            return;
+        }
+    }
+    update_body<T, T>(Wt, p.ld, slot, p.kk, row0, (const T2 *)p.zhat + (long long)w.y * KKMAX * KKMAX, smraw);
+}
+
+// The update route of every transformed pair of the pencils in FP64 sweeps
+// (route_class; 2 = the FP64 product for every pair when enable is 0).
+__global__ void route_batched(const BPencil *__restrict__ P, const BState *__restrict__ S,
+                              const int4 *__restrict__ work, int enable)
+{
+    const int4 w = work[blockIdx.x];
+    const BState st = S[w.x];
+    if (!st.active || st.pending || st.phase != 0) return;
+    const BPencil &p = P[w.x];
+    if (!p.flag[w.y]) return;
+    const int c = enable ? route_class(p.zhat + (long long)w.y * KKMAX * KKMAX, p.kk) : 2;
+    if (threadIdx.x == 0) p.route[w.y] = c;
 }
 
 // The round products W_i Z'_low,i -> Wtmp_i of the pencils listed in pend
@@ -296,7 +328,7 @@ long long a256(long long x) { return rup(x, 256); }
 struct PlanP {
     int m, p, n, m_pad, p_pad, n_pad, nb, wb, kk, npairs, nsteps, kc, chunks_h, chunks_s;
     long long Mt;
-    long long oW, oPart, oZhat, oFlag, oSlot, oJrow, oCnt, oErr, oLam, oGsc, oVn, oGc, oKap, oRank;
+    long long oW, oPart, oZhat, oFlag, oRoute, oSlot, oJrow, oCnt, oErr, oLam, oGsc, oVn, oGc, oKap, oRank;
     long long oTmp;             // W V0 (warm start) or W Z'_low (mixed schedule), or -1
     long long oW32;             // complex64 copy of W (mixed schedule), or -1
     int mixed;                  // this pencil runs the mixed schedule
@@ -365,6 +397,7 @@ Plan make_plan(int batch, const int64_t *m, const int64_t *p, const int64_t *n, 
         q.oPart = carve(16LL * q.npairs * cpp * hz::KKMAX * hz::KKMAX);
         q.oZhat = carve(16LL * q.npairs * hz::KKMAX * hz::KKMAX);
         q.oFlag = carve(4LL * q.npairs);
+        q.oRoute = carve(4LL * q.npairs);
         q.oSlot = carve(4LL * q.nsteps * q.npairs * q.kk);
         q.oJrow = carve(q.m_pad);
         q.oCnt = carve(16);
@@ -468,6 +501,7 @@ static ghsvd_status setup_batch(BatchBuffers &bb, const Plan &pl, int batch, con
         d.partial = (double2 *)(base + q.oPart);
         d.zhat = (double2 *)(base + q.oZhat);
         d.flag = (int *)(base + q.oFlag);
+        d.route = (int *)(base + q.oRoute);
         d.cnt = (unsigned long long *)(base + q.oCnt);
         d.err = (int *)(base + q.oErr);
         d.m_pad = q.m_pad; d.p_pad = q.p_pad; d.n_pad = q.n_pad; d.n = q.n;
@@ -614,6 +648,7 @@ static cudaError_t enqueue_tick(const BatchBuffers &bb, const Plan &pl, int batc
     if (mixed)
         hz::inner_batched<float><<<pl.inner_work, 1024, hz::inner_smem_bytes(sizeof(float2)), st>>>(
             bb.d_pen, bb.d_state, wi, o.inner_sweeps, o.crit_mode, o.mixed_param32);
+    hz::route_batched<<<pl.inner_work, 256, 0, st>>>(bb.d_pen, bb.d_state, wi, o.delta_update);
     hz::update_batched<double><<<pl.update_work, 256, hz::update_smem(sizeof(double2)), st>>>(
         bb.d_pen, bb.d_state, wu);
     if (mixed)
