@@ -285,8 +285,9 @@ void ghsvd_destroy(ghsvd_t h);
  * cores, mixed_tc is not used), each ended by the FP64 product W Z'_low in
  * the next tick, then FP64 sweeps to the stopping rule; a pencil given a V0
  * starts its first round from (F V0, G V0).  ghsvd_stats.sweeps_low and
- * rounds_low are the sums over the pencils.  delta_update is not used by
- * batched solves.
+ * rounds_low are the sums over the pencils.  delta_update applies to the
+ * FP64 sweeps of every pencil as in ghsvd_solve (the pairs_* statistics are
+ * not kept for batched solves).
  * Returns GHSVD_OK when every pencil converged, otherwise the status of the
  * first pencil that failed (or GHSVD_ERR_NOT_CONVERGED).
  */
