@@ -137,8 +137,9 @@ typedef struct {
                             bound about 2^-47 sum_l |x_il| per entry; typical
                             error that of the FP64 product), with all entries
                             <= 2^-11 in double-float arithmetic (FP32 pairs, 48
-                            significant bits; bound about 2^-52 sum_l |x_il|,
-                            typical error far below the FP64 product's).
+                            significant bits; bound about 2^-52 sum_l |x_il|;
+                            for a row of comparable entries its typical error
+                            is far below the FP64 product's).
                             The other pairs, and every pair with 0, by the FP64
                             product                                           */
 } ghsvd_opts;
@@ -390,6 +391,24 @@ ghsvd_status ghsvd_align_phases(int64_t n, const void *Vref, int64_t ldr, void *
  */
 ghsvd_status ghsvd_tc_block_ops(int64_t rows, void *X, int64_t ldx, const int8_t *J, const void *Z,
                                 void *gram, void *stream);
+
+/*
+ * The block update of the FP64 sweeps (Section 6.4.3) on one block pair, by
+ * one of its three routes, for verification against a reference:
+ * X <- X Z (route 2: the FP64 product, three-multiplication form), or in the
+ * delta form X <- X + X (Z - I) with the product in FP32 (route 0, used by
+ * the solve when every entry of Z - I is at most 2^-29) or in double-float
+ * arithmetic (route 1, at most 2^-11); the route is taken as given, whatever
+ * the size of Z - I.
+ *   X     device, complex128, rows x 64, column-major with ldx >= rows, rows a
+ *         positive multiple of 64; overwritten
+ *   Z     device, complex128 64 x 64, column-major (ld 64); in the delta forms
+ *         a column equal to e_j leaves column j of X exactly as it was
+ * Allocates its small temporaries on `stream`; returns INVALID_ARG for bad
+ * sizes, pointers or route.
+ */
+ghsvd_status ghsvd_fp64_block_update(int64_t rows, void *X, int64_t ldx, const void *Z, int route,
+                                     void *stream);
 
 /* Size of the device array that ghsvd_solve_noalloc works in (32 MiB). */
 #define GHSVD_NOALLOC_SCRATCH_BYTES (32u << 20)

@@ -22,6 +22,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "../../include/ghsvd.h"
 #include "hz_common.cuh"
 #include "hz_delta.cuh"
 #include "hz_launch.h"
@@ -101,4 +102,54 @@ cudaError_t launch_update_delta64(double2 *W, const StepArgs &a, const double2 *
     return cudaGetLastError();
 }
 
+namespace {
+
+__global__ void block_update_setup(int *slotcol, int *flag)
+{
+    const int t = threadIdx.x;
+    if (t < KKMAX) slotcol[t] = t;
+    if (t == 0) flag[0] = 1;
+}
+
+}  // namespace
 }  // namespace hz
+
+extern "C" ghsvd_status ghsvd_fp64_block_update(int64_t rows, void *X, int64_t ldx, const void *Z, int route,
+                                                void *stream)
+{
+    if (rows < 64 || rows % 64 != 0 || rows > (1 << 24) || ldx < rows || !X || !Z || route < 0 || route > 2)
+        return GHSVD_ERR_INVALID_ARG;
+    cudaPointerAttributes ax{}, az{};
+    if (cudaPointerGetAttributes(&ax, X) != cudaSuccess || cudaPointerGetAttributes(&az, Z) != cudaSuccess ||
+        ax.type != cudaMemoryTypeDevice || az.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return GHSVD_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (hz::delta64_setup() != cudaSuccess || hz::setup_kernels() != cudaSuccess) return GHSVD_ERR_CUDA;
+    int *slotcol = nullptr, *flag = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&slotcol, hz::KKMAX * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&flag, sizeof(int), st);
+    if (e == cudaSuccess) {
+        hz::block_update_setup<<<1, 64, 0, st>>>(slotcol, flag);
+        e = cudaGetLastError();
+    }
+    hz::StepArgs sa{};
+    sa.slotcol = slotcol;
+    sa.npairs = 1;
+    sa.kk = hz::KKMAX;
+    sa.m_pad = (int)rows;
+    sa.p_pad = 0;
+    sa.n_pad = 0;
+    sa.ld = ldx;
+    const double2 *zp = (const double2 *)Z;
+    if (e == cudaSuccess) {
+        if (route == 0) e = hz::launch_update_delta64((double2 *)X, sa, zp, flag, st);
+        else if (route == 1) e = hz::launch_update_df64((double2 *)X, sa, zp, flag, st);
+        else e = hz::launch_update(X, false, sa, zp, flag, st);
+    }
+    cudaFreeAsync(slotcol, st);
+    cudaFreeAsync(flag, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? GHSVD_OK : (e == cudaErrorMemoryAllocation ? GHSVD_ERR_NOMEM : GHSVD_ERR_CUDA);
+}

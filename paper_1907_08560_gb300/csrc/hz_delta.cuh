@@ -152,8 +152,10 @@ __device__ __forceinline__ void df_mac(float &sh, float &sl, float ah, float al,
 // renormalized sums about 2^-47 of the partial sum per step: at most about
 // 2^-41 sum_l |x_l||e_lj| <= 2^-52 sum_l |x_l| in all, about twice the FP64
 // product's own bound gamma_kk sum_l |x_l||z_lj| ~ 2^-47 |x_j| for a row of
-// comparable entries, and its typical (random-walk) error is far below the
-// FP64 product's.  The FP32 pipe of this GPU is 64 times its FP64 pipe: with
+// comparable entries, where its typical (random-walk) error is also far below
+// the FP64 product's.  (In a row whose other entries are far larger than
+// x_j the terms x_l e_lj dominate, and the product's 48-bit rounding of them
+// exceeds the FP64 product's.)  The FP32 pipe of this GPU is 64 times its FP64 pipe: with
 // 60 FP32 operations per complex multiply-add instead of 3 FP64 FMAs (the 3M
 // form), a pair costs about a third of its FP64 update.
 //

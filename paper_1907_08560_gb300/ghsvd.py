@@ -101,6 +101,8 @@ def load(path: str | None = None):
     lib.ghsvd_get_stats.argtypes = [vp, ctypes.POINTER(ghsvd_stats)]
     lib.ghsvd_tc_block_ops.restype = c_int
     lib.ghsvd_tc_block_ops.argtypes = [i64, vp, i64, vp, vp, vp, vp]
+    lib.ghsvd_fp64_block_update.restype = c_int
+    lib.ghsvd_fp64_block_update.argtypes = [i64, vp, i64, vp, c_int, vp]
     lib.ghsvd_solve_noalloc.restype = c_int
     lib.ghsvd_solve_noalloc.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, i64,
                                         ctypes.POINTER(ghsvd_opts), ctypes.POINTER(c_int), vp]
@@ -498,6 +500,21 @@ def ghsvd_tc_block_ops(X, J, Z, stream=None):
     _check(load().ghsvd_tc_block_ops(rows, X.data_ptr(), ld_of(X), Jp, Z.data_ptr(), gram.data_ptr(),
                                       _stream_ptr(stream)))
     return gram
+
+
+FP64_ROUTE_DELTA32, FP64_ROUTE_DOUBLE_FLOAT, FP64_ROUTE_FP64 = 0, 1, 2
+
+
+def ghsvd_fp64_block_update(X, Z, route, stream=None):
+    """The FP64 sweeps' block update of one pair by the given route
+    (include/ghsvd.h): X (rows x 64 complex128 column-major CUDA tensor, rows
+    a multiple of 64) is overwritten by X Z (route 2) or X + X (Z - I)
+    (route 0: FP32 product, route 1: double-float product)."""
+    import torch
+    if X.dtype != torch.complex128 or Z.dtype != torch.complex128:
+        raise TypeError("ghsvd_fp64_block_update works on complex128 tensors")
+    _check(load().ghsvd_fp64_block_update(X.shape[0], X.data_ptr(), ld_of(X), Z.data_ptr(), int(route),
+                                           _stream_ptr(stream)))
 
 
 def ghsvd_v0_targets(Vref, Vs, stream=None):
