@@ -1,12 +1,14 @@
 // Host-side rules of the CUDA library, printed for test_host_logic.py:
 // the Gram row chunk, the Gram CTA sizes, the shared-memory budgets and the
-// round-robin table of the step kernels (no GPU needed).
+// round-robin table of the step kernels, the sizes of the delta-form update
+// tiles (no GPU needed).
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 
 #include "../paper_1907_08560_gb300/csrc/hz_launch.h"
 #include "../paper_1907_08560_gb300/csrc/hz_pivot.cuh"
+#include "../paper_1907_08560_gb300/csrc/hz_delta.cuh"
 
 int main(int argc, char **argv)
 {
@@ -19,6 +21,11 @@ int main(int argc, char **argv)
                hz::update_smem(8), hz::inner_smem_bytes(16), hz::inner_smem_bytes(8));
         for (int kk = 2; kk <= hz::KKMAX; kk += 2)
             printf("threads %d %d %d\n", kk, hz::gram_threads(kk), hz::gram_threads_c128(kk));
+        return 0;
+    }
+    if (argc == 2 && !strcmp(argv[1], "delta")) {
+        printf("%zu %zu %zu %d %d %.17g %.17g\n", hz::delta64_smem(), hz::df64_smem(), hz::update_smem(16),
+               hz::UPD_R, hz::DF_R, hz::DELTA_E, hz::DF_E);
         return 0;
     }
     if (argc == 3 && !strcmp(argv[1], "rr")) {

@@ -84,3 +84,16 @@ def test_round_robin_table(prog, N):
         assert all(a < b for a, b in step)
         seen.update(step)
     assert len(seen) == N * (N - 1) // 2                              # every pair once a sweep
+
+
+def test_delta_update_tiles_fit(prog):
+    # the delta-form tiles of the FP64 sweeps: the double-float tile runs two
+    # CTAs per SM; the batched FP64 update runs either delta tile (and the
+    # double-float tile twice, on the two halves of a 64-row tile) inside the
+    # shared memory it is launched with for the FP64 product
+    d64, df, upd16, upd_r, df_r, delta_e, df_e = run(prog, "delta")[0].split()
+    d64, df, upd16, upd_r, df_r = map(int, (d64, df, upd16, upd_r, df_r))
+    assert upd_r == 2 * df_r
+    assert d64 <= upd16 and df <= upd16 <= SMEM_MAX
+    assert 2 * (df + 1024) <= 228 * 1024
+    assert float(delta_e) == 2.0 ** -29 and float(df_e) == 2.0 ** -11
