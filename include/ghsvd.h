@@ -386,8 +386,9 @@ ghsvd_status ghsvd_align_phases(int64_t n, const void *Vref, int64_t ldr, void *
  *   gram  device, complex64 64 x 64, column-major, written in full (the upper
  *         part computed, the lower part its conjugate transpose)
  * Allocates its small temporaries on `stream`; returns INVALID_ARG for bad
- * sizes, GHSVD_ERR_CUDA if the tensor-core path is not available or a
- * device-side wait ran out.
+ * sizes or for a pointer that is not device memory of the current device,
+ * GHSVD_ERR_CUDA if the tensor-core path is not available or a device-side
+ * wait ran out.
  */
 ghsvd_status ghsvd_tc_block_ops(int64_t rows, void *X, int64_t ldx, const int8_t *J, const void *Z,
                                 void *gram, void *stream);
@@ -405,7 +406,8 @@ ghsvd_status ghsvd_tc_block_ops(int64_t rows, void *X, int64_t ldx, const int8_t
  *   Z     device, complex128 64 x 64, column-major (ld 64); in the delta forms
  *         a column equal to e_j leaves column j of X exactly as it was
  * Allocates its small temporaries on `stream`; returns INVALID_ARG for bad
- * sizes, pointers or route.
+ * sizes or route, or for a pointer that is not device memory of the current
+ * device.
  */
 ghsvd_status ghsvd_fp64_block_update(int64_t rows, void *X, int64_t ldx, const void *Z, int route,
                                      void *stream);

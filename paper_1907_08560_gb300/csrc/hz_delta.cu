@@ -119,12 +119,17 @@ extern "C" ghsvd_status ghsvd_fp64_block_update(int64_t rows, void *X, int64_t l
 {
     if (rows < 64 || rows % 64 != 0 || rows > (1 << 24) || ldx < rows || !X || !Z || route < 0 || route > 2)
         return GHSVD_ERR_INVALID_ARG;
+    int dev = 0;
     cudaPointerAttributes ax{}, az{};
-    if (cudaPointerGetAttributes(&ax, X) != cudaSuccess || cudaPointerGetAttributes(&az, Z) != cudaSuccess ||
-        ax.type != cudaMemoryTypeDevice || az.type != cudaMemoryTypeDevice) {
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&ax, X) != cudaSuccess ||
+        cudaPointerGetAttributes(&az, Z) != cudaSuccess) {
         cudaGetLastError();
         return GHSVD_ERR_INVALID_ARG;
     }
+    auto dev_ok = [dev](const cudaPointerAttributes &p) {
+        return (p.type == cudaMemoryTypeDevice || p.type == cudaMemoryTypeManaged) && p.device == dev;
+    };
+    if (!dev_ok(ax) || !dev_ok(az)) return GHSVD_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     if (hz::delta64_setup() != cudaSuccess || hz::setup_kernels() != cudaSuccess) return GHSVD_ERR_CUDA;
     int *slotcol = nullptr, *flag = nullptr;

@@ -825,10 +825,29 @@ __global__ void tc_check_sum(const float2 *partial, int chunks, float2 *out)
 }  // namespace
 }  // namespace hz
 
+namespace {
+
+// p is device (or managed) memory of the current device
+bool on_current_device(const void *p)
+{
+    int dev = 0;
+    cudaPointerAttributes a{};
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
+}  // namespace
+
 extern "C" ghsvd_status ghsvd_tc_block_ops(int64_t rows, void *X, int64_t ldx, const int8_t *J, const void *Z,
                                            void *gram, void *stream)
 {
     if (rows < 64 || rows % 64 != 0 || rows > (1 << 24) || !X || !Z || !gram || ldx != rows)
+        return GHSVD_ERR_INVALID_ARG;
+    if (!on_current_device(X) || !on_current_device(Z) || !on_current_device(gram) ||
+        (J && !on_current_device(J)))
         return GHSVD_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     if (hz::tc_setup() != cudaSuccess || !hz::tc_supported(64, 1, ldx)) return GHSVD_ERR_CUDA;
