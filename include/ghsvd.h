@@ -306,6 +306,11 @@ ghsvd_status ghsvd_solve_batched(ghsvd_t h, int batch, const int64_t *m, const i
  * one.  For a family of pencils F(t), G(t) a small MLP trained on the
  * solver's own eigenvectors predicts V0(t); ghsvd_s_orthonormalize makes it
  * S-orthonormal; the sweeps then run to the stopping rule of Section 6.1.7.
+ * The array arguments of the calls below (but the parameter copies of
+ * ghsvd_mlp_get / ghsvd_mlp_set, which take host or device memory) must be
+ * device memory of the MLP's device, or of the current device for the calls
+ * without an MLP; any other pointer returns GHSVD_ERR_INVALID_ARG before
+ * anything is queued.
  * ------------------------------------------------------------------------ */
 typedef struct ghsvd_mlp *ghsvd_mlp_t;
 

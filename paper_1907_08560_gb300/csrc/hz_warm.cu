@@ -517,6 +517,19 @@ struct DevGuard {
     ~DevGuard() { cudaSetDevice(prev); }
 };
 
+// p is device (or managed) memory of `device` (-1: the current device).
+bool dev_ok(const void *p, int device = -1)
+{
+    if (!p) return false;
+    if (device < 0 && cudaGetDevice(&device) != cudaSuccess) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == device;
+}
+
 }  // namespace
 
 extern "C" {
@@ -599,7 +612,7 @@ ghsvd_status ghsvd_mlp_set(ghsvd_mlp_t m, const float *src)
 
 ghsvd_status ghsvd_mlp_forward(ghsvd_mlp_t m, int batch, const float *X, float *Y, void *stream)
 {
-    if (!m || batch < 1 || !X || !Y) return GHSVD_ERR_INVALID_ARG;
+    if (!m || batch < 1 || !dev_ok(X, m->device) || !dev_ok(Y, m->device)) return GHSVD_ERR_INVALID_ARG;
     DevGuard g(m->device);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = mlp_acts(m, batch);
@@ -611,7 +624,7 @@ ghsvd_status ghsvd_mlp_forward(ghsvd_mlp_t m, int batch, const float *X, float *
 ghsvd_status ghsvd_mlp_loss_grad(ghsvd_mlp_t m, int batch, const float *X, const float *T,
                                  double *loss, void *stream)
 {
-    if (!m || batch < 1 || !X || !T) return GHSVD_ERR_INVALID_ARG;
+    if (!m || batch < 1 || !dev_ok(X, m->device) || !dev_ok(T, m->device)) return GHSVD_ERR_INVALID_ARG;
     DevGuard g(m->device);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = mlp_acts(m, batch);
@@ -623,7 +636,8 @@ ghsvd_status ghsvd_mlp_loss_grad(ghsvd_mlp_t m, int batch, const float *X, const
 ghsvd_status ghsvd_mlp_train(ghsvd_mlp_t m, int n_samples, const float *X, const float *T,
                              int epochs, int batch, float lr, double *final_loss, void *stream)
 {
-    if (!m || n_samples < 1 || !X || !T || epochs < 1 || batch < 1 || !(lr > 0.f))
+    if (!m || n_samples < 1 || !dev_ok(X, m->device) || !dev_ok(T, m->device) || epochs < 1 || batch < 1 ||
+        !(lr > 0.f))
         return GHSVD_ERR_INVALID_ARG;
     DevGuard g(m->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -659,7 +673,7 @@ ghsvd_status ghsvd_s_orthonormalize(int count, int64_t p, int64_t n, const void 
     if (count < 1 || p < n || n < 1 || n > 4096 || !G || !V0 || !ldg || !ldv0)
         return GHSVD_ERR_INVALID_ARG;
     for (int i = 0; i < count; ++i)
-        if (!G[i] || !V0[i] || ldg[i] < p || ldv0[i] < n) return GHSVD_ERR_INVALID_ARG;
+        if (!dev_ok(G[i]) || !dev_ok(V0[i]) || ldg[i] < p || ldv0[i] < n) return GHSVD_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     // for every pair: X = G V0 (p x n), C = X^* X = L L^*, V0 <- V0 (L^{-1})^*;
     // each stage is one batched launch over all pairs
@@ -710,9 +724,10 @@ ghsvd_status ghsvd_s_orthonormalize(int count, int64_t p, int64_t n, const void 
 ghsvd_status ghsvd_v0_targets(int count, int64_t n, const void *Vref, int64_t ldr, const void *const *V,
                               const int64_t *ldv, float *T, double *rms, void *stream)
 {
-    if (count < 1 || n < 1 || n > 4096 || !Vref || ldr < n || !V || !ldv || !T) return GHSVD_ERR_INVALID_ARG;
+    if (count < 1 || n < 1 || n > 4096 || !dev_ok(Vref) || ldr < n || !V || !ldv || !dev_ok(T))
+        return GHSVD_ERR_INVALID_ARG;
     for (int i = 0; i < count; ++i)
-        if (!V[i] || ldv[i] < n) return GHSVD_ERR_INVALID_ARG;
+        if (!dev_ok(V[i]) || ldv[i] < n) return GHSVD_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const double2 **dV = nullptr;
     long long *dl = nullptr;
@@ -745,9 +760,10 @@ ghsvd_status ghsvd_v0_targets(int count, int64_t n, const void *Vref, int64_t ld
 ghsvd_status ghsvd_v0_compose(int count, int64_t n, const float *Y, double scale, const void *Vref, int64_t ldr,
                               void *const *V0, const int64_t *ldv0, void *stream)
 {
-    if (count < 1 || n < 1 || n > 4096 || !Y || !Vref || ldr < n || !V0 || !ldv0) return GHSVD_ERR_INVALID_ARG;
+    if (count < 1 || n < 1 || n > 4096 || !dev_ok(Y) || !dev_ok(Vref) || ldr < n || !V0 || !ldv0)
+        return GHSVD_ERR_INVALID_ARG;
     for (int i = 0; i < count; ++i)
-        if (!V0[i] || ldv0[i] < n) return GHSVD_ERR_INVALID_ARG;
+        if (!dev_ok(V0[i]) || ldv0[i] < n) return GHSVD_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     double2 **dV = nullptr;
     long long *dl = nullptr;
@@ -771,7 +787,7 @@ ghsvd_status ghsvd_v0_compose(int count, int64_t n, const float *Y, double scale
 ghsvd_status ghsvd_align_phases(int64_t n, const void *Vref, int64_t ldr, void *V, int64_t ldv,
                                 void *stream)
 {
-    if (n < 1 || !Vref || !V || ldr < n || ldv < n) return GHSVD_ERR_INVALID_ARG;
+    if (n < 1 || !dev_ok(Vref) || !dev_ok(V) || ldr < n || ldv < n) return GHSVD_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     align_phases<<<(unsigned)n, 256, 0, st>>>((const double2 *)Vref, ldr, (double2 *)V, ldv, (int)n);
     cudaError_t e = cudaGetLastError();
